@@ -1,0 +1,105 @@
+"""Pins of the oracle's determinant enumeration and product basis.
+
+Sources: Table I (App. A) for the bit representation and its order; the
+dimensions printed in the paper for the 20Ne sd space (640, App. C Fig. 8),
+24Mg sd space (28,503, App. C Fig. 9), 48Cr pf space (1,963,461, Sec. IV A)
+and 112Sn (6,210,638, Sec. IV C); closed forms for the number of one-body
+jumps.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import basis as ob
+from oracle import hamiltonian as oh
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_table1():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "table1.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        parts = line.split()
+        bits = [int(x) for x in parts[1:9]]
+        group = tuple(int(x) for x in parts[9].split(",")) if len(parts) > 9 else None
+        rows.append((int(parts[0]), bits, group))
+    return rows
+
+
+def test_table1_bit_rows_and_order():
+    sp = synth.make_space(synth.TABLE1_SHELLS)
+    got = ob.table1_order(sp.twom, sp.orbit, 3, 1)
+    want = _read_table1()
+    assert len(got) == len(want) == 9
+    prev_group = None
+    for (N, occ, bits), (serial, wbits, wgroup) in zip(got, want):
+        assert [bits >> i & 1 for i in range(8)] == wbits, serial
+        if wgroup is not None:
+            assert N == wgroup and N != prev_group
+        else:
+            assert N == prev_group
+        prev_group = N
+
+
+def test_table1_determinants_are_the_M_block():
+    sp = synth.make_space(synth.TABLE1_SHELLS)
+    dets = [b for (m, b) in ob.species_determinants(sp.twom, 3) if m == 1]
+    assert sorted(dets) == sorted(r[2] for r in ob.table1_order(sp.twom, sp.orbit, 3, 1))
+
+
+@pytest.mark.parametrize("k,want", [(2, 640), (4, 28503)])
+def test_paper_dimensions_sd_enumerated(k, want):
+    sp = synth.make_space(synth.SPACE12_SHELLS)
+    B = ob.ProductBasis(sp.twom, k, sp.twom, k, 0)
+    assert B.dim == want
+    assert len(set(B.states)) == want
+    for (SA, SB) in B.states[:: max(1, want // 200)]:
+        mA = sum(sp.twom[i] for i in range(sp.n) if SA >> i & 1)
+        mB = sum(sp.twom[i] for i in range(sp.n) if SB >> i & 1)
+        assert mA + mB == 0
+        assert SA.bit_count() == k and SB.bit_count() == k
+
+
+def test_paper_dimension_pf_48Cr():
+    sp = synth.make_space(synth.SPACE20_SHELLS)
+    L = oh.LazyIndex(sp.twom, 4, sp.twom, 4, 0)
+    assert L.dim == 1963461
+    assert len(L.detsA) == 4845
+
+
+def test_generating_function_matches_enumeration():
+    for shells, k1, k2, twoM in ((synth.SPACE12_SHELLS, 2, 2, 0), (synth.SPACE12_SHELLS, 3, 2, 1),
+                                 (synth.SPACE12_SHELLS, 4, 4, 0), (synth.TABLE1_SHELLS, 3, 0, 1),
+                                 (synth.SPACE12_SHELLS, 1, 0, 3)):
+        sp = synth.make_space(shells)
+        B = ob.ProductBasis(sp.twom, k1, sp.twom, k2, twoM)
+        assert B.dim == ob.dimension_by_generating_function(sp.twom, k1, sp.twom, k2, twoM)
+
+
+def test_generating_function_paper_dimensions():
+    sp20 = synth.make_space(synth.SPACE20_SHELLS)
+    assert ob.dimension_by_generating_function(sp20.twom, 4, sp20.twom, 4, 0) == 1963461
+    # 112Sn: 12 neutrons in g7/2 d5/2 d3/2 s1/2 h11/2, M = 0, positive parity.
+    sn = synth.make_space(((7, 0), (5, 0), (3, 0), (1, 0), (11, 0)))
+    parity = [1 if o == 4 else 0 for o in sn.orbit]
+    assert ob.dimension_by_generating_function((), 0, sn.twom, 12, 0, parity, 0) == 6210638
+
+
+def test_one_body_jump_closed_form():
+    sp = synth.make_space(synth.SPACE12_SHELLS)
+    for k in (1, 2, 3, 4):
+        ndet = len(ob.species_determinants(sp.twom, k))
+        assert ob.one_body_jump_count(sp.twom, k) == ndet * k * (sp.n - k)
+
+
+def test_species_order_is_M_then_value():
+    sp = synth.make_space(synth.SPACE12_SHELLS)
+    dets = ob.species_determinants(sp.twom, 3)
+    keys = [(m, b) for m, b in dets]
+    assert keys == sorted(keys)
+    for m, b in dets:
+        assert m == sum(sp.twom[i] for i in range(sp.n) if b >> i & 1)
