@@ -1,0 +1,219 @@
+/*
+ * trbl.h -- C ABI of the GB300 thick-restart block Lanczos library for
+ * M-scheme shell-model Hamiltonians (Shimizu, Mizusaki, Utsuno, Tsunoda,
+ * "Thick-restart block Lanczos method for large-scale shell-model
+ * calculations", arXiv 1902.02064).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Return value: TRBL_OK (0) or a TRBL_ERR_* status.  No C++ exception
+ *   crosses this boundary.  trbl_last_error() returns a message for the last
+ *   failing call on the calling thread (thread-local, owned by the library,
+ *   valid until the next failing call on that thread).
+ * - "Host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *   global memory of the current device.  The caller owns every buffer it
+ *   passes; the library owns the objects it creates (trbl_basis,
+ *   trbl_hamiltonian) and frees them in the matching *_destroy call.
+ * - Streams are passed as `void*` holding a cudaStream_t (NULL = legacy
+ *   default stream).  Work is enqueued asynchronously on that stream unless
+ *   an entry point says it synchronises.
+ * - A model space of one species lists its single-particle m-states in a
+ *   fixed order; bit i of a determinant's bit string is m-state i
+ *   (Sec. II Eq. (mbasis); App. A Table I).  At most 32 m-states per species.
+ * - Species determinants are ordered by ascending 2M and, within equal 2M,
+ *   by the unsigned value of the bit string.  The product basis (App. A
+ *   Eq. (part)) is a sequence of blocks, one per 2M_A (ascending) for which
+ *   both species have determinants with 2M_A + 2M_B = 2M; inside a block the
+ *   state (iA, iB) has index offset + iA * N_B + iB.
+ * - A block of vectors is row-major: row i (basis state i) holds q values,
+ *   rows ld elements apart (ld >= q).
+ */
+#ifndef TRBL_H
+#define TRBL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TRBL_OK 0
+#define TRBL_ERR_ARG 1       /* invalid argument (null pointer, size, layout) */
+#define TRBL_ERR_CUDA 2      /* a CUDA runtime or library call failed */
+#define TRBL_ERR_OOM 3       /* device or host allocation failed */
+#define TRBL_ERR_BREAKDOWN 4 /* block QR found a rank-deficient block it could not repair */
+#define TRBL_ERR_NOCONV 5    /* iteration limit reached; partial results returned */
+
+#define TRBL_F32 0 /* IEEE binary32 vectors */
+#define TRBL_F64 1 /* IEEE binary64 vectors */
+
+/* One species' single-particle space: n_states m-states with their 2j, 2m and
+ * shell index, occupied by n_particles particles.  Arrays are host memory of
+ * length n_states, read during the call only. */
+typedef struct trbl_space {
+  int n_states;
+  const int* twoj;
+  const int* twom;
+  const int* orbit;
+  int n_particles;
+} trbl_space;
+
+typedef struct trbl_basis trbl_basis;
+typedef struct trbl_hamiltonian trbl_hamiltonian;
+
+/* Sizes of a basis, filled by trbl_basis_info. */
+typedef struct trbl_basis_sizes {
+  int64_t dim;          /* M-scheme dimension D */
+  int32_t n_det[2];     /* determinants of species A, B (all 2M) */
+  int32_t n_blocks;     /* product blocks */
+  int64_t n_jumps[2];   /* one-body jump entries of A, B, diagonal a=c included */
+  int32_t n_delta;      /* number of 2m-transfer classes, 2*span/2+1 */
+} trbl_basis_sizes;
+
+/* Builds the two-species M-scheme basis of total 2M = twoM: determinant
+ * enumeration (Sec. II Eq. (mbasis)), the product blocks of App. A
+ * Eq. (part), and the one-body jump lists of App. B.2 (every
+ * a+_a a_c |S> with its target, source and sign; the paper stores them per
+ * partition, here per target determinant and 2m transfer).  Host-only work:
+ * it needs no GPU.  *out is owned by the library.
+ * Errors: TRBL_ERR_ARG for null pointers, more than 32 m-states, particle
+ * numbers outside [0, n_states], or an empty basis. */
+int trbl_basis_create(const trbl_space* A, const trbl_space* B, int twoM, trbl_basis** out);
+
+/* Frees a basis.  The caller must destroy every Hamiltonian built on it first. */
+void trbl_basis_destroy(trbl_basis* b);
+
+/* Fills *sizes.  Host-only. */
+int trbl_basis_info(const trbl_basis* b, trbl_basis_sizes* sizes);
+
+/* Copies the basis description into caller-owned host arrays (any may be
+ * NULL to skip it): bitsA/twoMA [n_det[0]], bitsB/twoMB [n_det[1]], and
+ * blocks [n_blocks * 7] as rows (2M_A, 2M_B, offset, N_A, N_B, first A
+ * determinant, first B determinant).  Host-only. */
+int trbl_basis_export(const trbl_basis* b, uint32_t* bitsA, int32_t* twoMA, uint32_t* bitsB,
+                      int32_t* twoMB, int64_t* blocks);
+
+/* Copies the one-body jump list of one species (0 = A, 1 = B) into
+ * caller-owned host arrays of length n_jumps[species]: jump e maps source
+ * determinant src[e] to target tgt[e] by a+_{a[e]} a_{c[e]} with fermion sign
+ * sign[e] (+1/-1), global determinant indices (App. B.2, the "one-body
+ * jumps").  Diagonal entries a = c (number operators) are included.
+ * Entries are ordered by target, then 2m transfer, then source.  Host-only. */
+int trbl_basis_export_jumps(const trbl_basis* b, int species, int32_t* tgt, int32_t* src,
+                            int32_t* a, int32_t* c, int8_t* sign);
+
+/* Builds the device tables of H = H1 + H2 (Sec. II) on the current CUDA
+ * device: like-particle target lists with their summed coefficients
+ * (App. B.1) and the cross-species coefficient table used with the jump
+ * lists (App. B.2 Eq. (pntwobodybit)).  Inputs are host FP64 arrays, read
+ * during the call only:
+ *   h1A[nA*nA]  h(1)_ac of a+_a a_c for species A (row a, column c);
+ *   h1B[nB*nB]  the same for species B;
+ *   VAA[nA^4]   h(2)_abcd of a+_a a+_b a_d a_c, index ((a*nA+b)*nA+c)*nA+d,
+ *               read only for a<b, c<d;
+ *   VBB[nB^4]   the same for species B;
+ *   VAB[nA*nB*nA*nB] coefficient of a+_a b+_b b_d a_c, index
+ *               ((a*nB+b)*nA+c)*nB+d.
+ * Coefficients that do not conserve 2m are ignored.  The caller keeps b
+ * alive while *out exists.  Errors: TRBL_ERR_ARG, TRBL_ERR_OOM,
+ * TRBL_ERR_CUDA. */
+int trbl_hamiltonian_create(const trbl_basis* b, const double* h1A, const double* h1B,
+                            const double* VAA, const double* VBB, const double* VAB,
+                            trbl_hamiltonian** out);
+
+/* Frees the Hamiltonian's device tables (synchronises the device first). */
+void trbl_hamiltonian_destroy(trbl_hamiltonian* h);
+
+/* W = H V for a block of q vectors (Alg. 3/4 line "W := H V_k"), matrix
+ * elements generated on the fly from the jump lists (App. B).  V and W are
+ * device arrays of D rows, leading dimensions ldv, ldw >= q, element type
+ * dtype (TRBL_F32 or TRBL_F64, accumulation in that type).  W is
+ * overwritten; V and W must not overlap.  1 <= q <= 64.  Asynchronous on
+ * stream.  Errors: TRBL_ERR_ARG, TRBL_ERR_CUDA (launch failure). */
+int trbl_apply_block(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, int64_t ldw,
+                     int q, int dtype, void* stream);
+
+#define TRBL_PREC_F64 1   /* FP64 vectors, apply and projections */
+#define TRBL_PREC_MIXED 2 /* FP32 vectors and apply; FP64 CGS2 coefficients, CholQR2, Ritz */
+
+/* Solver parameters (Alg. 4).  Zero fields take the documented defaults. */
+typedef struct trbl_params {
+  int nev;             /* wanted lowest eigenpairs */
+  int q;               /* block size p of the paper, 1..64 */
+  int max_basis;       /* l_m: Lanczos vectors kept before a thick restart */
+  int keep;            /* l_s: Ritz vectors kept at a restart; 0 = nev + (max_basis-nev)/4,
+                          clipped to max_basis - 2q */
+  double tol;          /* converged when ||beta_k U_{last q rows,i}|| <= tol * ||H|| for i < nev */
+  int precision;       /* TRBL_PREC_F64 or TRBL_PREC_MIXED */
+  int max_iter;        /* block iterations cap; 0 = 100000 */
+  int check_every;     /* Rayleigh-Ritz convergence test every this many block steps; 0 = 1 */
+  uint64_t seed;       /* start block: uniform(-1,1) from splitmix64(seed<<32 + i*q + j) */
+  double normH;        /* ||H|| used by tol; 0 = estimated by the solver (largest |Ritz value|) */
+} trbl_params;
+
+/* Per-solve statistics (per-phase times mirror the paper's Fig. 5(c)). */
+typedef struct trbl_stats {
+  int iterations;      /* block Lanczos steps (applications of H to a block) */
+  int restarts;        /* thick restarts */
+  int converged;       /* eigenpairs meeting the tolerance */
+  int status;          /* return value of trbl_solve */
+  double normH;        /* ||H|| used by the tolerance */
+  double ms_total, ms_apply, ms_orth, ms_qr, ms_ritz, ms_restart;
+} trbl_stats;
+
+/* Lowest nev eigenpairs of H by the thick-restart block Lanczos method
+ * (Sec. III D, Alg. 4, restart of Eq. (trb-tmat)), with full
+ * reorthogonalisation (classical Gram-Schmidt applied twice) against every
+ * stored Lanczos vector and Cholesky-QR applied twice as the block QR.
+ * Outputs: evals[nev] (host, ascending), resid[nev] (host, true residual
+ * norms ||H x - theta x|| recomputed with a fresh FP64 apply, may be NULL),
+ * evecs (device, D x nev row-major FP64 in TRBL_PREC_F64 and FP32 in mixed
+ * mode, may be NULL), *stats (host, may be NULL).  Allocates its own device
+ * workspace (basis of D x max_basis) and synchronises the stream before it
+ * returns.  Errors: TRBL_ERR_ARG, TRBL_ERR_OOM, TRBL_ERR_CUDA,
+ * TRBL_ERR_BREAKDOWN, TRBL_ERR_NOCONV (outputs then hold the best current
+ * approximations). */
+int trbl_solve(const trbl_hamiltonian* h, const trbl_params* p, double* evals, double* resid,
+               void* evecs, trbl_stats* stats, void* stream);
+
+/* Stepwise form of trbl_solve for callers that drive the iteration
+ * themselves.  A solver owns its device workspace (basis of D x max_basis
+ * vectors plus O(D q) blocks) and runs every call on the stream given here;
+ * calls synchronise that stream before they return.
+ *
+ * trbl_solver_create: validates p (copied), allocates, and builds the
+ *   orthonormal start block (Alg. 4, first line).  Errors as trbl_solve.
+ * trbl_solver_step: one block step of Alg. 4 -- W := H V_k, alpha_k,
+ *   full reorthogonalisation, V_{k+1} beta_k := QR(W), Rayleigh-Ritz when due
+ *   (every check_every steps and before every restart) -- followed by a thick
+ *   restart (Eq. (trb-tmat)) when the basis is full.  *converged (may be
+ *   NULL) receives the number of converged pairs when a Rayleigh-Ritz test
+ *   ran in this step, else -1.  After convergence further steps do nothing.
+ * trbl_solver_step_host: the same step with the current block V_k read from
+ *   host memory block_in (D x q, row-major, element type of the precision:
+ *   FP64 or FP32; NULL keeps the device copy) before the step and the next
+ *   block written to host memory block_out (same layout; NULL skips) after
+ *   it.  Pinned host memory makes the copies asynchronous.
+ * trbl_solver_block: device address and byte size of the current block V_k
+ *   (D x q row-major), valid until the next step.
+ * trbl_solver_stats: statistics so far (ms_total counts from creation).
+ * trbl_solver_finish: Ritz values (ascending), true residuals and Ritz
+ *   vectors of the current basis, as trbl_solve returns them; TRBL_ERR_NOCONV
+ *   when not all nev pairs met the tolerance (outputs still filled).
+ * trbl_solver_destroy: synchronises the stream and frees the solver. */
+typedef struct trbl_solver trbl_solver;
+int trbl_solver_create(const trbl_hamiltonian* h, const trbl_params* p, void* stream, trbl_solver** out);
+int trbl_solver_step(trbl_solver* s, int* converged);
+int trbl_solver_step_host(trbl_solver* s, const void* block_in, void* block_out, int* converged);
+int trbl_solver_block(trbl_solver* s, void** block, int64_t* bytes);
+int trbl_solver_stats(trbl_solver* s, trbl_stats* stats);
+int trbl_solver_finish(trbl_solver* s, double* evals, double* resid, void* evecs, trbl_stats* stats);
+void trbl_solver_destroy(trbl_solver* s);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* trbl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRBL_H */

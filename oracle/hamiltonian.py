@@ -252,3 +252,22 @@ def hv_rows_lazy(L: LazyIndex, T: TermTables, V: np.ndarray, rows) -> np.ndarray
         for v, A2, B2 in column_terms(SA, SB, T):
             out[k] += v * V[L.index(A2, B2)].astype(np.float64)
     return out
+
+
+def one_body_jumps(twom, k: int):
+    """Every one-body jump a+_a a_c |S> = sign |S'> of one species (App. B.2,
+    the "one-body jumps"), diagonal a = c included, as a set of
+    (target index, source index, a, c, sign) with the species' sorted
+    determinant indices."""
+    from .basis import species_determinants
+    dets = species_determinants(twom, k)
+    where = {b: i for i, (_, b) in enumerate(dets)}
+    n = len(twom)
+    out = set()
+    for i, (_, S) in enumerate(dets):
+        for c in range(n):
+            for a in range(n):
+                s, A2, _ = apply_string(S, 0, ((0, True, a), (0, False, c)))
+                if s:
+                    out.add((where[A2], i, a, c, s))
+    return out

@@ -1,0 +1,23 @@
+"""GB300 thick-restart block Lanczos for M-scheme shell-model Hamiltonians.
+
+Thin Python binding of the C-ABI library libtrbl.so (declared in
+include/trbl.h): argument marshalling only.  Every step of the computation
+runs in the library's CUDA kernels; there is no CPU fallback.  PyTorch is
+used for device memory and streams.
+
+Method: Shimizu, Mizusaki, Utsuno, Tsunoda, arXiv 1902.02064 -- the
+thick-restart block Lanczos method (Sec. III D, Alg. 4) with the on-the-fly
+block product H V on a proton-neutron factorised M-scheme basis (App. A,
+App. B).
+"""
+from ._lib import (  # noqa: F401
+    TRBL_OK, TRBL_ERR_ARG, TRBL_ERR_CUDA, TRBL_ERR_OOM, TRBL_ERR_BREAKDOWN, TRBL_ERR_NOCONV,
+    TRBL_F32, TRBL_F64, TRBL_PREC_F64, TRBL_PREC_MIXED, TrblError,
+    lib, library_path,
+    trbl_basis_create, trbl_basis_destroy, trbl_basis_info, trbl_basis_export,
+    trbl_basis_export_jumps, trbl_hamiltonian_create, trbl_hamiltonian_destroy,
+    trbl_apply_block, trbl_solve, trbl_last_error,
+    trbl_solver_create, trbl_solver_step, trbl_solver_step_host, trbl_solver_block,
+    trbl_solver_stats, trbl_solver_destroy,
+    Basis, Hamiltonian, Solver, solve,
+)

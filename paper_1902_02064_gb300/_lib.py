@@ -1,0 +1,365 @@
+"""ctypes binding of libtrbl.so: same names as the C entry points, plus two
+small owning wrappers (Basis, Hamiltonian) and ``solve``."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+TRBL_OK, TRBL_ERR_ARG, TRBL_ERR_CUDA, TRBL_ERR_OOM, TRBL_ERR_BREAKDOWN, TRBL_ERR_NOCONV = range(6)
+TRBL_F32, TRBL_F64 = 0, 1
+TRBL_PREC_F64, TRBL_PREC_MIXED = 1, 2
+
+
+class TrblError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("trbl error %d: %s" % (code, msg))
+        self.code = code
+
+
+class trbl_space(C.Structure):
+    _fields_ = [("n_states", C.c_int), ("twoj", C.POINTER(C.c_int)), ("twom", C.POINTER(C.c_int)),
+                ("orbit", C.POINTER(C.c_int)), ("n_particles", C.c_int)]
+
+
+class trbl_basis_sizes(C.Structure):
+    _fields_ = [("dim", C.c_int64), ("n_det", C.c_int32 * 2), ("n_blocks", C.c_int32),
+                ("n_jumps", C.c_int64 * 2), ("n_delta", C.c_int32)]
+
+
+class trbl_params(C.Structure):
+    _fields_ = [("nev", C.c_int), ("q", C.c_int), ("max_basis", C.c_int), ("keep", C.c_int),
+                ("tol", C.c_double), ("precision", C.c_int), ("max_iter", C.c_int),
+                ("check_every", C.c_int), ("seed", C.c_uint64), ("normH", C.c_double)]
+
+
+class trbl_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
+                ("status", C.c_int), ("normH", C.c_double), ("ms_total", C.c_double),
+                ("ms_apply", C.c_double), ("ms_orth", C.c_double), ("ms_qr", C.c_double),
+                ("ms_ritz", C.c_double), ("ms_restart", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+_VP = C.c_void_p
+_DP = C.POINTER(C.c_double)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libtrbl.so, building it first when a source is newer.  Raises if it
+    cannot be built or loaded: there is no fallback path."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.build()
+    L = C.CDLL(path)
+    sig = {
+        "trbl_basis_create": (C.c_int, [C.POINTER(trbl_space), C.POINTER(trbl_space), C.c_int, C.POINTER(_VP)]),
+        "trbl_basis_destroy": (None, [_VP]),
+        "trbl_basis_info": (C.c_int, [_VP, C.POINTER(trbl_basis_sizes)]),
+        "trbl_basis_export": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+        "trbl_basis_export_jumps": (C.c_int, [_VP, C.c_int, _VP, _VP, _VP, _VP, _VP]),
+        "trbl_hamiltonian_create": (C.c_int, [_VP, _DP, _DP, _DP, _DP, _DP, C.POINTER(_VP)]),
+        "trbl_hamiltonian_destroy": (None, [_VP]),
+        "trbl_apply_block": (C.c_int, [_VP, _VP, C.c_int64, _VP, C.c_int64, C.c_int, C.c_int, _VP]),
+        "trbl_solve": (C.c_int, [_VP, C.POINTER(trbl_params), _DP, _DP, _VP, C.POINTER(trbl_stats), _VP]),
+        "trbl_solver_create": (C.c_int, [_VP, C.POINTER(trbl_params), _VP, C.POINTER(_VP)]),
+        "trbl_solver_step": (C.c_int, [_VP, C.POINTER(C.c_int)]),
+        "trbl_solver_step_host": (C.c_int, [_VP, _VP, _VP, C.POINTER(C.c_int)]),
+        "trbl_solver_block": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(C.c_int64)]),
+        "trbl_solver_stats": (C.c_int, [_VP, C.POINTER(trbl_stats)]),
+        "trbl_solver_finish": (C.c_int, [_VP, _DP, _DP, _VP, C.POINTER(trbl_stats)]),
+        "trbl_solver_destroy": (None, [_VP]),
+        "trbl_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = L
+    return L
+
+
+def trbl_last_error() -> str:
+    return lib().trbl_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != TRBL_OK:
+        raise TrblError(rc, trbl_last_error())
+
+
+def _iarr(x: Sequence[int]):
+    a = (C.c_int * len(x))(*[int(v) for v in x])
+    return a
+
+
+def _space(sp, k: int):
+    """trbl_space from an object with twoj/twom/orbit sequences (e.g. synth.ModelSpace)."""
+    tj, tm, ob = _iarr(sp.twoj), _iarr(sp.twom), _iarr(sp.orbit)
+    s = trbl_space(len(sp.twom), tj, tm, ob, int(k))
+    return s, (tj, tm, ob)
+
+
+def _f64(a: np.ndarray):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_DP)
+
+
+# ---- raw entry points (same names as the C ABI) ------------------------------
+
+def trbl_basis_create(spaceA, kA: int, spaceB, kB: int, twoM: int) -> int:
+    sA, keepA = _space(spaceA, kA)
+    sB, keepB = _space(spaceB, kB)
+    out = _VP()
+    _check(lib().trbl_basis_create(C.byref(sA), C.byref(sB), int(twoM), C.byref(out)))
+    return out.value
+
+
+def trbl_basis_destroy(b: int):
+    lib().trbl_basis_destroy(b)
+
+
+def trbl_basis_info(b: int) -> dict:
+    s = trbl_basis_sizes()
+    _check(lib().trbl_basis_info(b, C.byref(s)))
+    return {"dim": s.dim, "n_det": (s.n_det[0], s.n_det[1]), "n_blocks": s.n_blocks,
+            "n_jumps": (s.n_jumps[0], s.n_jumps[1]), "n_delta": s.n_delta}
+
+
+def trbl_basis_export(b: int):
+    info = trbl_basis_info(b)
+    nA, nB = info["n_det"]
+    bitsA = np.zeros(nA, np.uint32)
+    mA = np.zeros(nA, np.int32)
+    bitsB = np.zeros(nB, np.uint32)
+    mB = np.zeros(nB, np.int32)
+    blocks = np.zeros((info["n_blocks"], 7), np.int64)
+    _check(lib().trbl_basis_export(b, bitsA.ctypes.data, mA.ctypes.data, bitsB.ctypes.data,
+                                   mB.ctypes.data, blocks.ctypes.data))
+    return bitsA, mA, bitsB, mB, blocks
+
+
+def trbl_basis_export_jumps(b: int, species: int):
+    n = trbl_basis_info(b)["n_jumps"][species]
+    tgt, src, a, c = (np.zeros(n, np.int32) for _ in range(4))
+    sign = np.zeros(n, np.int8)
+    _check(lib().trbl_basis_export_jumps(b, int(species), tgt.ctypes.data, src.ctypes.data,
+                                         a.ctypes.data, c.ctypes.data, sign.ctypes.data))
+    return tgt, src, a, c, sign
+
+
+def trbl_hamiltonian_create(b: int, h1A, h1B, VAA, VBB, VAB) -> int:
+    arrs = [_f64(x) for x in (h1A, h1B, VAA, VBB, VAB)]
+    out = _VP()
+    _check(lib().trbl_hamiltonian_create(b, *[p for _, p in arrs], C.byref(out)))
+    return out.value
+
+
+def trbl_hamiltonian_destroy(h: int):
+    lib().trbl_hamiltonian_destroy(h)
+
+
+def trbl_apply_block(h: int, V_ptr: int, ldv: int, W_ptr: int, ldw: int, q: int, dtype: int,
+                     stream: int = 0):
+    _check(lib().trbl_apply_block(h, V_ptr, int(ldv), W_ptr, int(ldw), int(q), int(dtype), stream))
+
+
+def trbl_solve(h: int, params: trbl_params, evals_ptr, resid_ptr, evecs_ptr: int,
+               stats: trbl_stats, stream: int = 0) -> int:
+    rc = lib().trbl_solve(h, C.byref(params), evals_ptr, resid_ptr, evecs_ptr, C.byref(stats), stream)
+    return rc
+
+
+# ---- owning wrappers ---------------------------------------------------------
+
+class Basis:
+    """Two-species M-scheme basis built by the library (host-side tables)."""
+
+    def __init__(self, spaceA, kA: int, spaceB, kB: int, twoM: int):
+        self.handle = None
+        self.handle = trbl_basis_create(spaceA, kA, spaceB, kB, twoM)
+        self.info = trbl_basis_info(self.handle)
+        self.dim = self.info["dim"]
+
+    def export(self):
+        return trbl_basis_export(self.handle)
+
+    def export_jumps(self, species: int):
+        return trbl_basis_export_jumps(self.handle, species)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.trbl_basis_destroy(self.handle)
+            self.handle = None
+
+
+class Hamiltonian:
+    """Device tables of H on a Basis (current CUDA device)."""
+
+    def __init__(self, basis: Basis, h1A, h1B, VAA, VBB, VAB):
+        self.handle = None
+        self.basis = basis
+        self.handle = trbl_hamiltonian_create(basis.handle, h1A, h1B, VAA, VBB, VAB)
+
+    @classmethod
+    def from_interaction(cls, basis: Basis, inter):
+        return cls(basis, inter.h1A, inter.h1B, inter.VAA, inter.VBB, inter.VAB)
+
+    def apply(self, V, W=None, stream=None):
+        """W = H V for a torch CUDA tensor V of shape (D, q), float32 or float64."""
+        import torch
+        if V.dim() != 2 or V.shape[0] != self.basis.dim or V.stride(1) != 1:
+            raise ValueError("V must be (D, q) with unit column stride")
+        if not V.is_cuda:
+            raise ValueError("V must be a CUDA tensor")
+        if V.dtype == torch.float64:
+            dt = TRBL_F64
+        elif V.dtype == torch.float32:
+            dt = TRBL_F32
+        else:
+            raise ValueError("V must be float32 or float64")
+        if W is None:
+            W = torch.empty_like(V, memory_format=torch.contiguous_format)
+        if W.shape != V.shape or W.dtype != V.dtype or W.stride(1) != 1:
+            raise ValueError("W must match V's shape and dtype with unit column stride")
+        s = stream if stream is not None else torch.cuda.current_stream(V.device)
+        trbl_apply_block(self.handle, V.data_ptr(), V.stride(0), W.data_ptr(), W.stride(0),
+                         V.shape[1], dt, s.cuda_stream)
+        return W
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.trbl_hamiltonian_destroy(self.handle)
+            self.handle = None
+
+
+def solve(h: Hamiltonian, nev: int, q: int, max_basis: int, tol: float,
+          precision: int = TRBL_PREC_F64, keep: int = 0, max_iter: int = 0,
+          check_every: int = 0, seed: int = 1, normH: float = 0.0, want_vectors: bool = True,
+          stream=None, raise_on_noconv: bool = True):
+    """Lowest nev eigenpairs by trbl_solve.  Returns (evals, resid, evecs or None, stats dict)."""
+    import torch
+    D = h.basis.dim
+    p = trbl_params(int(nev), int(q), int(max_basis), int(keep), float(tol), int(precision),
+                    int(max_iter), int(check_every), int(seed), float(normH))
+    st = trbl_stats()
+    ev = np.zeros(nev)
+    rs = np.zeros(nev)
+    X = None
+    if want_vectors:
+        dt = torch.float64 if precision == TRBL_PREC_F64 else torch.float32
+        X = torch.empty((D, nev), dtype=dt, device="cuda")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = trbl_solve(h.handle, p, ev.ctypes.data_as(_DP), rs.ctypes.data_as(_DP),
+                    X.data_ptr() if X is not None else None, st, s.cuda_stream)
+    if rc != TRBL_OK and not (rc == TRBL_ERR_NOCONV and not raise_on_noconv):
+        raise TrblError(rc, trbl_last_error())
+    d = st.as_dict()
+    d["rc"] = rc
+    return ev, rs, X, d
+
+
+def _params(nev, q, max_basis, tol, precision=TRBL_PREC_F64, keep=0, max_iter=0, check_every=0, seed=1,
+            normH=0.0):
+    return trbl_params(int(nev), int(q), int(max_basis), int(keep), float(tol), int(precision),
+                       int(max_iter), int(check_every), int(seed), float(normH))
+
+
+def trbl_solver_create(h: int, params: trbl_params, stream: int = 0) -> int:
+    out = _VP()
+    _check(lib().trbl_solver_create(h, C.byref(params), stream, C.byref(out)))
+    return out.value
+
+
+def trbl_solver_step(sv: int) -> int:
+    c = C.c_int(-1)
+    _check(lib().trbl_solver_step(sv, C.byref(c)))
+    return c.value
+
+
+def trbl_solver_step_host(sv: int, block_in: int, block_out: int) -> int:
+    c = C.c_int(-1)
+    _check(lib().trbl_solver_step_host(sv, block_in, block_out, C.byref(c)))
+    return c.value
+
+
+def trbl_solver_block(sv: int):
+    p = _VP()
+    n = C.c_int64()
+    _check(lib().trbl_solver_block(sv, C.byref(p), C.byref(n)))
+    return p.value, n.value
+
+
+def trbl_solver_stats(sv: int) -> dict:
+    st = trbl_stats()
+    _check(lib().trbl_solver_stats(sv, C.byref(st)))
+    return st.as_dict()
+
+
+def trbl_solver_destroy(sv: int):
+    lib().trbl_solver_destroy(sv)
+
+
+class Solver:
+    """Stepwise thick-restart block Lanczos (trbl_solver_* entry points)."""
+
+    def __init__(self, h: Hamiltonian, nev: int, q: int, max_basis: int, tol: float,
+                 precision: int = TRBL_PREC_F64, keep: int = 0, check_every: int = 0, seed: int = 1,
+                 normH: float = 0.0, stream=None):
+        import torch
+        self.h = h
+        self.nev, self.q, self.precision = nev, q, precision
+        self.handle = None
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        self.params = _params(nev, q, max_basis, tol, precision, keep, 0, check_every, seed, normH)
+        self.handle = trbl_solver_create(h.handle, self.params, s.cuda_stream)
+
+    def step(self) -> int:
+        return trbl_solver_step(self.handle)
+
+    def step_host(self, block_in, block_out) -> int:
+        """One step with V_k read from / V_{k+1} written to host tensors (pinned for speed)."""
+        return trbl_solver_step_host(self.handle, block_in.data_ptr() if block_in is not None else None,
+                                     block_out.data_ptr() if block_out is not None else None)
+
+    def block(self):
+        return trbl_solver_block(self.handle)
+
+    def stats(self) -> dict:
+        return trbl_solver_stats(self.handle)
+
+    def finish(self, want_vectors: bool = True, raise_on_noconv: bool = True):
+        import torch
+        D = self.h.basis.dim
+        ev = np.zeros(self.nev)
+        rs = np.zeros(self.nev)
+        X = None
+        if want_vectors:
+            dt = torch.float64 if self.precision == TRBL_PREC_F64 else torch.float32
+            X = torch.empty((D, self.nev), dtype=dt, device="cuda")
+        st = trbl_stats()
+        rc = lib().trbl_solver_finish(self.handle, ev.ctypes.data_as(_DP), rs.ctypes.data_as(_DP),
+                                      X.data_ptr() if X is not None else None, C.byref(st))
+        if rc != TRBL_OK and not (rc == TRBL_ERR_NOCONV and not raise_on_noconv):
+            raise TrblError(rc, trbl_last_error())
+        d = st.as_dict()
+        d["rc"] = rc
+        return ev, rs, X, d
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.trbl_solver_destroy(self.handle)
+            self.handle = None

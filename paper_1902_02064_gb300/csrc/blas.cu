@@ -1,0 +1,277 @@
+// Tall-skinny dense kernels of the block Lanczos step (Sec. III C/D):
+//   * block_dot:  C = B^T W  (m x q coefficients of W against m stored
+//     vectors; Alg. 3/4 "alpha_k := V_k^T W" and the reorthogonalisation),
+//   * rowgemm:    Out = alpha * In U + beta * Out  (W -= B C in the
+//     reorthogonalisation, W R^{-1} in the block QR, and the restart
+//     compression v_k := sum_j v_j U_jk of Sec. III D),
+//   * column copies, casts and the seeded start block.
+// Vectors are row-major D x ld.  Small matrices (C, U, R) are FP64.
+// In FP32 storage the products are FP32 FMAs summed in two FP32 levels per
+// thread block, and the per-block partial sums are reduced across blocks in
+// FP64 in a fixed order (deterministic).
+#include "blas.cuh"
+
+namespace trbl {
+
+namespace {
+
+constexpr int MT = 128;  // stored vectors per block_dot tile
+
+template <typename T>
+struct DotCfg;
+template <>
+struct DotCfg<float> {
+  static constexpr int RS = 32;  // rows per shared-memory stage
+};
+template <>
+struct DotCfg<double> {
+  static constexpr int RS = 16;
+};
+
+// partial[chunk][i][j] = sum over the chunk's rows r of B[r, m0+i] W[r, j]
+// grid = (m tiles, row chunks); threads = 32 x (QP/4); thread (tm, tq)
+// owns b-columns 4tm..4tm+3 and w-columns 4tq..4tq+3.
+template <typename T, int QP>
+__global__ void __launch_bounds__(32 * (QP / 4)) block_dot_kernel(
+    const T* __restrict__ B, int64_t ldb, int m, const T* __restrict__ W, int64_t ldw, int q,
+    int64_t D, int64_t rows_per_chunk, double* __restrict__ partial) {
+  constexpr int RS = DotCfg<T>::RS;
+  constexpr int NT = 32 * (QP / 4);
+  __shared__ __align__(16) T Bs[RS][MT];
+  __shared__ __align__(16) T Ws[RS][QP];
+  const int tid = threadIdx.x;
+  const int tm = tid & 31, tq = tid >> 5;
+  const int m0 = blockIdx.x * MT;
+  const int64_t r_begin = int64_t(blockIdx.y) * rows_per_chunk;
+  const int64_t r_end = min(D, r_begin + rows_per_chunk);
+  T acc[4][4];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += RS) {
+    for (int idx = tid; idx < RS * MT; idx += NT) {
+      const int rr = idx / MT, cc = idx - rr * MT;
+      const int64_t r = r0 + rr;
+      Bs[rr][cc] = (r < r_end && m0 + cc < m) ? B[r * ldb + m0 + cc] : T(0);
+    }
+    for (int idx = tid; idx < RS * QP; idx += NT) {
+      const int rr = idx / QP, cc = idx - rr * QP;
+      const int64_t r = r0 + rr;
+      Ws[rr][cc] = (r < r_end && cc < q) ? W[r * ldw + cc] : T(0);
+    }
+    __syncthreads();
+    T t[4][4];
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) t[i][j] = T(0);
+#pragma unroll 4
+    for (int rr = 0; rr < RS; ++rr) {
+      T b[4], w[4];
+      for (int i = 0; i < 4; ++i) b[i] = Bs[rr][4 * tm + i];
+      for (int j = 0; j < 4; ++j) w[j] = Ws[rr][4 * tq + j];
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) t[i][j] = fma(b[i], w[j], t[i][j]);
+    }
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) acc[i][j] += t[i][j];
+    __syncthreads();
+  }
+  double* P = partial + int64_t(blockIdx.y) * m * q;
+  for (int i = 0; i < 4; ++i) {
+    const int bi = m0 + 4 * tm + i;
+    if (bi >= m) continue;
+    for (int j = 0; j < 4; ++j) {
+      const int wj = 4 * tq + j;
+      if (wj < q) P[int64_t(bi) * q + wj] = double(acc[i][j]);
+    }
+  }
+}
+
+__global__ void reduce_partials_kernel(const double* __restrict__ partial, int nchunk, int mq,
+                                       double* __restrict__ C) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= mq) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += partial[int64_t(c) * mq + i];
+  C[i] = s;
+}
+
+// Out[r, c] = alpha * sum_k In[r, k] U[k, c] + beta * Out[r, c]
+// Tile RT rows x CT columns, k staged KC at a time; thread owns 4 x 4.
+template <typename T, int RT, int CT>
+__global__ void __launch_bounds__(RT * CT / 16) rowgemm_kernel(
+    const T* __restrict__ In, int64_t ldi, int K, const double* __restrict__ U, int64_t ldu, int n,
+    T* __restrict__ Out, int64_t ldo, int64_t D, double alpha, double beta) {
+  constexpr int KC = 32;
+  constexpr int NT = RT * CT / 16;
+  constexpr int TR = RT / 4;
+  __shared__ __align__(16) T Bs[KC][RT + 4];
+  __shared__ __align__(16) T Us[KC][CT];
+  const int tid = threadIdx.x;
+  const int tr = tid % TR, tc = tid / TR;
+  const int64_t r0 = int64_t(blockIdx.x) * RT;
+  const int c0 = blockIdx.y * CT;
+  T acc[4][4];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    for (int idx = tid; idx < RT * KC; idx += NT) {
+      const int rr = idx / KC, kk = idx - rr * KC;
+      const int64_t r = r0 + rr;
+      Bs[kk][rr] = (r < D && k0 + kk < K) ? In[r * ldi + k0 + kk] : T(0);
+    }
+    for (int idx = tid; idx < KC * CT; idx += NT) {
+      const int kk = idx / CT, cc = idx - kk * CT;
+      Us[kk][cc] = (k0 + kk < K && c0 + cc < n) ? T(U[int64_t(k0 + kk) * ldu + c0 + cc]) : T(0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KC; ++kk) {
+      T b[4], u[4];
+      for (int i = 0; i < 4; ++i) b[i] = Bs[kk][4 * tr + i];
+      for (int j = 0; j < 4; ++j) u[j] = Us[kk][4 * tc + j];
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(b[i], u[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  for (int i = 0; i < 4; ++i) {
+    const int64_t r = r0 + 4 * tr + i;
+    if (r >= D) continue;
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + 4 * tc + j;
+      if (c >= n) continue;
+      T* o = Out + r * ldo + c;
+      const T v = T(alpha) * acc[i][j];
+      *o = (beta == 0.0) ? v : fma(T(beta), *o, v);
+    }
+  }
+}
+
+template <typename S, typename T>
+__global__ void copy_cols_kernel(const S* __restrict__ src, int64_t lds, T* __restrict__ dst,
+                                 int64_t ldd, int64_t D, int ncol) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t r = i / ncol;
+  const int c = int(i - r * ncol);
+  if (r >= D) return;
+  dst[r * ldd + c] = T(src[r * lds + c]);
+}
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// X[r, c] = 2u - 1 with u = top 53 bits of splitmix64((seed<<32) + r*ncol_total + col0 + c)
+template <typename T>
+__global__ void random_block_kernel(T* __restrict__ X, int64_t ldx, int64_t D, int ncol,
+                                    int ncol_total, int col0, uint64_t seed) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t r = i / ncol;
+  const int c = int(i - r * ncol);
+  if (r >= D) return;
+  const uint64_t ctr = ((seed & 0xffffffffull) << 32) + uint64_t(r) * ncol_total + col0 + c;
+  const double u = double(splitmix64(ctr) >> 11) * (1.0 / 9007199254740992.0);
+  X[r * ldx + c] = T(2.0 * u - 1.0);
+}
+
+template <typename T, int QP>
+int dot_launch(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, int64_t D,
+               double* C, Workspace& ws, cudaStream_t s) {
+  constexpr int RS = DotCfg<T>::RS;
+  const int mtiles = (m + MT - 1) / MT;
+  const int target = 4 * ws.sm_count;
+  int64_t nchunk = (target + mtiles - 1) / mtiles;
+  const int64_t max_chunks = (D + RS - 1) / RS;
+  if (nchunk > max_chunks) nchunk = max_chunks;
+  if (nchunk < 1) nchunk = 1;
+  int64_t rows = (D + nchunk - 1) / nchunk;
+  rows = (rows + RS - 1) / RS * RS;
+  nchunk = (D + rows - 1) / rows;
+  const size_t need = size_t(nchunk) * m * q * sizeof(double);
+  if (need > ws.partial_bytes) return fail(TRBL_ERR_ARG, "block_dot workspace too small");
+  dim3 grid(mtiles, unsigned(nchunk));
+  block_dot_kernel<T, QP><<<grid, 32 * (QP / 4), 0, s>>>(B, ldb, m, W, ldw, q, D, rows, ws.partial);
+  TRBL_CUDA(cudaGetLastError());
+  const int mq = m * q;
+  reduce_partials_kernel<<<(mq + 255) / 256, 256, 0, s>>>(ws.partial, int(nchunk), mq, C);
+  TRBL_CUDA(cudaGetLastError());
+  return TRBL_OK;
+}
+
+}  // namespace
+
+size_t block_dot_workspace_bytes(int m, int q, int sm_count) {
+  const int mtiles = (m + MT - 1) / MT;
+  const int64_t nchunk = (4 * sm_count + mtiles - 1) / mtiles + 1;
+  return size_t(nchunk) * m * q * sizeof(double);
+}
+
+template <typename T>
+int block_dot(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, int64_t D, double* C,
+              Workspace& ws, cudaStream_t s) {
+  if (m <= 0) return TRBL_OK;
+  if (q <= 4) return dot_launch<T, 4>(B, ldb, m, W, ldw, q, D, C, ws, s);
+  if (q <= 8) return dot_launch<T, 8>(B, ldb, m, W, ldw, q, D, C, ws, s);
+  if (q <= 16) return dot_launch<T, 16>(B, ldb, m, W, ldw, q, D, C, ws, s);
+  if (q <= 32) return dot_launch<T, 32>(B, ldb, m, W, ldw, q, D, C, ws, s);
+  if (q <= 64) return dot_launch<T, 64>(B, ldb, m, W, ldw, q, D, C, ws, s);
+  return fail(TRBL_ERR_ARG, "block_dot: q=%d > 64", q);
+}
+
+template <typename T>
+int rowgemm(const T* In, int64_t ldi, int K, const double* U, int64_t ldu, int n, T* Out,
+            int64_t ldo, int64_t D, double alpha, double beta, cudaStream_t s) {
+  if (n <= 0 || D <= 0) return TRBL_OK;
+  if (K <= 0) {
+    // Out = beta * Out
+    if (beta == 1.0) return TRBL_OK;
+  }
+  if (n <= 16) {
+    constexpr int RT = 128, CT = 16;
+    dim3 grid(unsigned((D + RT - 1) / RT), unsigned((n + CT - 1) / CT));
+    rowgemm_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta);
+  } else if (n <= 32) {
+    constexpr int RT = 128, CT = 32;
+    dim3 grid(unsigned((D + RT - 1) / RT), unsigned((n + CT - 1) / CT));
+    rowgemm_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta);
+  } else {
+    constexpr int RT = 64, CT = 64;
+    dim3 grid(unsigned((D + RT - 1) / RT), unsigned((n + CT - 1) / CT));
+    rowgemm_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta);
+  }
+  TRBL_CUDA(cudaGetLastError());
+  return TRBL_OK;
+}
+
+template <typename S, typename T>
+int copy_cols(const S* src, int64_t lds, T* dst, int64_t ldd, int64_t D, int ncol, cudaStream_t s) {
+  if (ncol <= 0 || D <= 0) return TRBL_OK;
+  const int64_t n = D * ncol;
+  copy_cols_kernel<S, T><<<unsigned((n + 255) / 256), 256, 0, s>>>(src, lds, dst, ldd, D, ncol);
+  TRBL_CUDA(cudaGetLastError());
+  return TRBL_OK;
+}
+
+template <typename T>
+int random_block(T* X, int64_t ldx, int64_t D, int ncol, int ncol_total, int col0, uint64_t seed,
+                 cudaStream_t s) {
+  const int64_t n = D * ncol;
+  random_block_kernel<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(X, ldx, D, ncol, ncol_total, col0, seed);
+  TRBL_CUDA(cudaGetLastError());
+  return TRBL_OK;
+}
+
+template int block_dot<float>(const float*, int64_t, int, const float*, int64_t, int, int64_t, double*, Workspace&, cudaStream_t);
+template int block_dot<double>(const double*, int64_t, int, const double*, int64_t, int, int64_t, double*, Workspace&, cudaStream_t);
+template int rowgemm<float>(const float*, int64_t, int, const double*, int64_t, int, float*, int64_t, int64_t, double, double, cudaStream_t);
+template int rowgemm<double>(const double*, int64_t, int, const double*, int64_t, int, double*, int64_t, int64_t, double, double, cudaStream_t);
+template int copy_cols<float, float>(const float*, int64_t, float*, int64_t, int64_t, int, cudaStream_t);
+template int copy_cols<double, double>(const double*, int64_t, double*, int64_t, int64_t, int, cudaStream_t);
+template int copy_cols<float, double>(const float*, int64_t, double*, int64_t, int64_t, int, cudaStream_t);
+template int copy_cols<double, float>(const double*, int64_t, float*, int64_t, int64_t, int, cudaStream_t);
+template int random_block<float>(float*, int64_t, int64_t, int, int, int, uint64_t, cudaStream_t);
+template int random_block<double>(double*, int64_t, int64_t, int, int, int, uint64_t, cudaStream_t);
+
+}  // namespace trbl

@@ -1,0 +1,39 @@
+// Tall-skinny dense kernels used by the solver (blas.cu).
+#pragma once
+
+#include "internal.h"
+
+namespace trbl {
+
+// Device scratch of the dense kernels (owned by the caller).
+struct Workspace {
+  double* partial = nullptr;  // block_dot partial sums
+  size_t partial_bytes = 0;
+  int sm_count = 152;
+};
+
+// Bytes of Workspace::partial needed by block_dot with these m, q.
+size_t block_dot_workspace_bytes(int m, int q, int sm_count);
+
+// C[m x q] (FP64, row-major, ld q) = B[:, 0:m]^T W[:, 0:q] over D rows.
+template <typename T>
+int block_dot(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, int64_t D, double* C,
+              Workspace& ws, cudaStream_t s);
+
+// Out[:, 0:n] = alpha * In[:, 0:K] U[K x n] + beta * Out (U FP64 row-major, ld ldu).
+// In and Out must not overlap.
+template <typename T>
+int rowgemm(const T* In, int64_t ldi, int K, const double* U, int64_t ldu, int n, T* Out,
+            int64_t ldo, int64_t D, double alpha, double beta, cudaStream_t s);
+
+// dst[:, 0:ncol] = src[:, 0:ncol] (with type conversion).
+template <typename S, typename T>
+int copy_cols(const S* src, int64_t lds, T* dst, int64_t ldd, int64_t D, int ncol, cudaStream_t s);
+
+// Seeded uniform(-1, 1) block: entry (r, col0 + c) uses counter
+// (seed << 32) + r * ncol_total + col0 + c through splitmix64.
+template <typename T>
+int random_block(T* X, int64_t ldx, int64_t D, int ncol, int ncol_total, int col0, uint64_t seed,
+                 cudaStream_t s);
+
+}  // namespace trbl

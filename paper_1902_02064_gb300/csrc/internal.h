@@ -1,0 +1,113 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/trbl.h"
+
+namespace trbl {
+
+// Records a message for trbl_last_error() and returns `code`.
+int fail(int code, const char* fmt, ...);
+// Clears the thread's error message (start of every entry point).
+void clear_error();
+// TRBL_ERR_CUDA with the call site and CUDA's message when e != cudaSuccess.
+int cuda_fail(cudaError_t e, const char* what);
+
+#define TRBL_CUDA(call)                                                  \
+  do {                                                                   \
+    cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) return ::trbl::cuda_fail(e_, #call);          \
+  } while (0)
+
+// One species of the two-species basis.
+struct Species {
+  int n = 0, k = 0;
+  std::vector<int> twom;
+  std::vector<uint32_t> bits;   // determinants, sorted by (2M, value)
+  std::vector<int32_t> dM;      // 2M of each determinant
+  std::vector<int32_t> group;   // determinant -> group index
+  std::vector<int32_t> gM, gfirst, gcount;  // groups of equal 2M, ascending
+  // One-body jumps gathered by target: entries of target t with 2m transfer
+  // index di are [jseg[t*ND+di], jseg[t*ND+di+1]).
+  std::vector<int32_t> jseg;
+  std::vector<int32_t> jsrc;    // global source determinant
+  std::vector<int32_t> ja, jc;  // a+_a a_c
+  std::vector<int8_t> jsign;
+  int find(uint32_t b, int M) const;  // global index or -1
+  int group_of_M(int M) const;        // group index or -1
+};
+
+struct Block {
+  int mA, mB;
+  int64_t off;
+  int na, nb;
+  int gA, gB;  // group indices in species A and B
+};
+
+}  // namespace trbl
+
+struct trbl_basis {
+  trbl::Species sp[2];
+  int twoM = 0;
+  int dspan = 0;  // 2m transfers lie in [-dspan, dspan]
+  int ND = 1;     // 2*dspan + 1
+  std::vector<trbl::Block> blocks;
+  std::vector<int32_t> srcblk;  // [blk*ND + di]: block holding M_A - delta, or -1
+  int64_t D = 0;
+};
+
+namespace trbl {
+
+// Device-side tables of one Hamiltonian (all pointers are device memory).
+template <typename T>
+struct DevH {
+  int nblk, ND, nA, nB;
+  const int64_t* boff;
+  const int32_t* bnb;
+  const int32_t* bgA;   // first A determinant of the block's A group
+  const int32_t* bgB;
+  const int32_t* srcblk;
+  // one-body jumps by target: (source local index, op = (a*n+c)<<1 | negative)
+  const int32_t* jsegA;
+  const int2* jA;
+  const int32_t* jsegB;
+  const int2* jB;
+  // like-particle H rows by target determinant: source local index, coefficient
+  const int32_t* hoffA;
+  const int32_t* hsrcA;
+  const T* hcoefA;
+  const int32_t* hoffB;
+  const int32_t* hsrcB;
+  const T* hcoefB;
+  // cross-species table vab[(a*nA+c)*nB*nB + b*nB+d] = V^AB_{ab,cd}
+  const T* vab;
+};
+
+}  // namespace trbl
+
+struct trbl_hamiltonian {
+  const trbl_basis* b = nullptr;
+  int device = 0;
+  // host copies of the like-particle rows (by target, global determinant index)
+  std::vector<int32_t> hoff[2], hsrc[2];
+  std::vector<double> hcoef[2];
+  std::vector<double> vab;  // (a*nA+c)*nB*nB + b*nB+d
+  // device allocations (one arena)
+  void* arena = nullptr;
+  trbl::DevH<double> d64;
+  trbl::DevH<float> d32;
+  size_t arena_bytes = 0;
+};
+
+namespace trbl {
+// Uploads the tables of h to the current device (apply.cu).
+int upload_tables(trbl_hamiltonian* h);
+// Enqueues W = H V (apply.cu).
+int launch_apply(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, int64_t ldw,
+                 int q, int dtype, cudaStream_t s);
+}  // namespace trbl

@@ -1,0 +1,773 @@
+// Thick-restart block Lanczos solver (Sec. III D, Alg. 4) on one GPU.
+//
+// Per block step k (Alg. 4 inner loop):
+//   W := H V_k                          on-the-fly block product (apply.cu)
+//   alpha_k := V_k^T W                  first Gram-Schmidt pass coefficients
+//   orthogonalise W against every stored Lanczos vector: classical
+//     Gram-Schmidt applied twice (the full reorthogonalisation of Sec. III)
+//   V_{k+1} beta_k := QR(W)             Cholesky QR applied twice, FP64 Gram
+//   T gets alpha_k on its block diagonal and beta_k below/above it
+//     (Eq. (tmat-blan); after a restart the arrow form of Eq. (trb-tmat))
+//   Rayleigh-Ritz: eigenpairs (theta_i, U_i) of T; the residual of Ritz
+//     pair i is ||beta_k U_{last q rows, i}||
+// When the basis would exceed max_basis (l_m) vectors, restart: keep the
+// l_s lowest Ritz vectors v_i := sum_j v_j U_ji, put V_{k_m+1} after them,
+// and rebuild T as diag(theta_1..l_s) bordered by r = beta_{k_m} U_{last
+// q rows, 1:l_s} (Eq. (trb-tmat) and the restart formulas below it).
+//
+// The paper leaves the QR method open; this uses Cholesky QR twice with
+// the Gram matrix in FP64.  A column whose Cholesky pivot falls below a
+// threshold (an exhausted Krylov direction) is replaced by a fresh seeded
+// random vector, the block is re-orthogonalised, and beta_k = V_{k+1}^T W.
+// The small symmetric eigenproblem uses cuSOLVER's syevd (FP64).
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <type_traits>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "blas.cuh"
+
+namespace trbl {
+namespace {
+
+#define TRBL_SOLVER(call)                                                         \
+  do {                                                                            \
+    cusolverStatus_t s_ = (call);                                                 \
+    if (s_ != CUSOLVER_STATUS_SUCCESS)                                            \
+      return fail(TRBL_ERR_CUDA, "%s: cusolver status %d", #call, int(s_));       \
+  } while (0)
+
+#define TRY(...)                \
+  do {                          \
+    int rc_ = (__VA_ARGS__);    \
+    if (rc_) return rc_;        \
+  } while (0)
+
+// Cholesky G = R^T R (R upper) of a q x q FP64 Gram matrix, R^{-1}, and
+// per-column deficiency flags: pivot^2 <= thresh2[j] marks column j.
+// One block of 64 threads; flags[0] counts deficient columns, flags[1+j] marks them.
+__global__ void chol_kernel(const double* __restrict__ G, int q, double thresh_abs, double thresh_rel,
+                            double* __restrict__ R, double* __restrict__ Rinv, int* __restrict__ flags) {
+  __shared__ double Rs[64][65];
+  __shared__ double diag0[64];
+  const int t = threadIdx.x;
+  for (int i = t; i < q * q; i += blockDim.x) {
+    const int r = i / q, c = i - r * q;
+    Rs[r][c] = (c >= r) ? G[i] : 0.0;
+  }
+  if (t < q) diag0[t] = G[t * q + t];
+  if (t == 0) flags[0] = 0;
+  if (t < q) flags[1 + t] = 0;
+  __syncthreads();
+  for (int j = 0; j < q; ++j) {
+    if (t == 0) {
+      double d = Rs[j][j];
+      for (int k = 0; k < j; ++k) d -= Rs[k][j] * Rs[k][j];
+      const double lim = fmax(thresh_abs * thresh_abs, thresh_rel * thresh_rel * fmax(diag0[j], 0.0));
+      if (!(d > lim)) {
+        flags[0] += 1;
+        flags[1 + j] = 1;
+        d = fmax(fabs(diag0[j]), 1e-300);
+      }
+      Rs[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    if (t > j && t < q) {
+      double s = Rs[j][t];
+      for (int k = 0; k < j; ++k) s -= Rs[k][j] * Rs[k][t];
+      Rs[j][t] = s / Rs[j][j];
+    }
+    __syncthreads();
+  }
+  for (int i = t; i < q * q; i += blockDim.x) {
+    const int r = i / q, c = i - r * q;
+    R[i] = (c >= r) ? Rs[r][c] : 0.0;
+  }
+  // column t of R^{-1} by back substitution
+  if (t < q) {
+    double x[64];
+    for (int j = t + 1; j < q; ++j) x[j] = 0.0;
+    for (int j = t; j >= 0; --j) {
+      double s = (j == t) ? 1.0 : 0.0;
+      for (int k = j + 1; k <= t; ++k) s -= Rs[j][k] * x[k];
+      x[j] = s / Rs[j][j];
+    }
+    for (int j = 0; j < q; ++j) Rinv[j * q + t] = (j <= t) ? x[j] : 0.0;
+  }
+}
+
+// beta = R2 R1 (both upper triangular, q x q row-major)
+__global__ void upper_mul_kernel(const double* __restrict__ R2, const double* __restrict__ R1, int q,
+                                 double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= q * q) return;
+  const int r = i / q, c = i - r * q;
+  double s = 0.0;
+  for (int k = r; k <= c; ++k) s += R2[r * q + k] * R1[k * q + c];
+  out[i] = (c >= r) ? s : 0.0;
+}
+
+// T[b0+i][b0+j] = (C[(b0+i)*q + j] + C[(b0+j)*q + i]) / 2
+__global__ void set_alpha_kernel(double* __restrict__ T, int ldt, const double* __restrict__ C, int b0, int q) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= q * q) return;
+  const int r = i / q, c = i - r * q;
+  T[int64_t(b0 + r) * ldt + b0 + c] = 0.5 * (C[(b0 + r) * q + c] + C[(b0 + c) * q + r]);
+}
+
+// T[r0+i][c0+j] = beta[i][j], T[c0+j][r0+i] = beta[i][j]
+__global__ void set_beta_kernel(double* __restrict__ T, int ldt, const double* __restrict__ beta, int r0,
+                                int c0, int q) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= q * q) return;
+  const int r = i / q, c = i - r * q;
+  const double v = beta[i];
+  T[int64_t(r0 + r) * ldt + c0 + c] = v;
+  T[int64_t(c0 + c) * ldt + r0 + r] = v;
+}
+
+// res[i] = || beta U[nb-q : nb, i] ||  for i < n (U column-major, ld ldu)
+__global__ void ritz_resid_kernel(const double* __restrict__ beta, int q, const double* __restrict__ U,
+                                  int ldu, int nb, int n, double* __restrict__ res) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double* u = U + int64_t(i) * ldu + (nb - q);
+  double s2 = 0.0;
+  for (int a = 0; a < q; ++a) {
+    double s = 0.0;
+    for (int b = 0; b < q; ++b) s += beta[a * q + b] * u[b];
+    s2 += s * s;
+  }
+  res[i] = sqrt(s2);
+}
+
+// Ut[k][c] = U(k, c) for k < nb, c < n: column-major (ld ldu) -> row-major (ld n)
+__global__ void transpose_kernel(const double* __restrict__ U, int ldu, int nb, int n, double* __restrict__ Ut) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb * n) return;
+  const int k = i / n, c = i - k * n;
+  Ut[i] = U[int64_t(c) * ldu + k];
+}
+
+// Thick-restart T (Eq. (trb-tmat)): diag(theta[0:ls]) bordered by
+// r[a][i] = sum_b beta[a][b] U[nb-q+b][i] in rows/cols ls..ls+q-1.
+__global__ void restart_t_kernel(double* __restrict__ T, int ldt, const double* __restrict__ theta,
+                                 const double* __restrict__ beta, int q, const double* __restrict__ U,
+                                 int ldu, int nb, int ls) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ls) T[int64_t(i) * ldt + i] = theta[i];
+  if (i >= ls * q) return;
+  const int a = i / ls, c = i - a * ls;
+  const double* u = U + int64_t(c) * ldu + (nb - q);
+  double s = 0.0;
+  for (int b = 0; b < q; ++b) s += beta[a * q + b] * u[b];
+  T[int64_t(ls + a) * ldt + c] = s;
+  T[int64_t(c) * ldt + ls + a] = s;
+}
+
+// Per-column partial sums of ||HX - theta X||^2 over a row chunk.
+__global__ void resid_partial_kernel(const double* __restrict__ HX, const double* __restrict__ X, int n,
+                                     const double* __restrict__ theta, int64_t D, int64_t rows,
+                                     double* __restrict__ part) {
+  const int c = threadIdx.x;
+  if (c >= n) return;
+  const int64_t r0 = int64_t(blockIdx.x) * rows, r1 = min(D, r0 + rows);
+  const double th = theta[c];
+  double s = 0.0;
+  for (int64_t r = r0; r < r1; ++r) {
+    const double d = HX[r * n + c] - th * X[r * n + c];
+    s += d * d;
+  }
+  part[int64_t(blockIdx.x) * n + c] = s;
+}
+
+__global__ void resid_final_kernel(const double* __restrict__ part, int nchunk, int n, double* __restrict__ out) {
+  const int c = threadIdx.x;
+  if (c >= n) return;
+  double s = 0.0;
+  for (int k = 0; k < nchunk; ++k) s += part[int64_t(k) * n + c];
+  out[c] = sqrt(s);
+}
+
+// Layout of the small int buffer shared by device and pinned host memory.
+constexpr int kF1 = 0;     // pass-1 Cholesky: count, then one flag per column
+constexpr int kF2 = 80;    // pass-2 Cholesky
+constexpr int kInfo = 160; // syevd info
+constexpr int kFlagInts = 192;
+
+// Host-side progress trace, on when the environment sets TRBL_TRACE=1.
+static bool trace_on() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = getenv("TRBL_TRACE");
+    on = (e && e[0] == '1') ? 1 : 0;
+  }
+  return on == 1;
+}
+static void trace(const char* fmt, ...) {
+  if (!trace_on()) return;
+  va_list ap;
+  va_start(ap, fmt);
+  fprintf(stderr, "[trbl] ");
+  vfprintf(stderr, fmt, ap);
+  fprintf(stderr, "\n");
+  fflush(stderr);
+  va_end(ap);
+}
+
+struct Timer {
+  cudaEvent_t ev[8];
+  bool on = false;
+  int init(bool want) {
+    on = want;
+    if (!on) return TRBL_OK;
+    for (auto& e : ev) TRBL_CUDA(cudaEventCreate(&e));
+    return TRBL_OK;
+  }
+  void rec(int i, cudaStream_t s) {
+    if (on) cudaEventRecord(ev[i], s);
+  }
+  double ms(int a, int b) {
+    if (!on) return 0.0;
+    float x = 0.f;
+    cudaEventElapsedTime(&x, ev[a], ev[b]);
+    return x;
+  }
+  ~Timer() {
+    if (on)
+      for (auto& e : ev) cudaEventDestroy(e);
+  }
+};
+
+struct Arena {
+  void* base = nullptr;
+  size_t off = 0, cap = 0;
+  template <typename X>
+  X* take(size_t n) {
+    size_t o = (off + 255) & ~size_t(255);
+    off = o + n * sizeof(X);
+    return reinterpret_cast<X*>(static_cast<char*>(base) + o);
+  }
+  ~Arena() {
+    if (base) cudaFree(base);
+  }
+};
+
+template <typename T>
+struct Solver {
+  const trbl_hamiltonian* h;
+  const trbl_params* p;
+  cudaStream_t s;
+  int64_t D;
+  int q, nev, mb, ls, dtype;
+  double tau;  // pass-1 deficiency threshold relative to ||H||
+  Workspace ws;
+  Arena ar;
+  T *basis, *Vk, *W, *W2, *Wsave, *panel;
+  int64_t panel_rows;
+  double *C, *G, *R1, *R1i, *R2, *R2i, *beta, *Tm, *Aw, *theta, *Ut, *res, *syev_work, *Xd, *HXd, *rpart, *rtrue;
+  int *flags, *devinfo;
+  int lwork;
+  int64_t nchunk_res;
+  cusolverDnHandle_t sol = nullptr;
+  double *hbuf;  // pinned: theta[mb], res[mb], flags as doubles
+  int* hflags;
+  uint64_t reseed = 0;
+  double normH = 0.0;
+
+  ~Solver() {
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (sol) cusolverDnDestroy(sol);
+    if (hbuf) cudaFreeHost(hbuf);
+    if (syev_work) cudaFree(syev_work);
+  }
+
+  int apply(const T* V, T* Wout) { return launch_apply(h, V, q, Wout, q, q, dtype, s); }
+
+  // W -= B[:, 0:nb] (B^T W), twice
+  int cgs2(T* Wb, int nb, double* Cout_first) {
+    if (nb == 0) return TRBL_OK;
+    TRY(block_dot<T>(basis, mb, nb, Wb, q, q, D, C, ws, s));
+    if (Cout_first && Cout_first != C)
+      TRBL_CUDA(cudaMemcpyAsync(Cout_first, C, sizeof(double) * nb * q, cudaMemcpyDeviceToDevice, s));
+    TRY(rowgemm<T>(basis, mb, nb, C, q, q, Wb, q, D, -1.0, 1.0, s));
+    TRY(block_dot<T>(basis, mb, nb, Wb, q, q, D, C + size_t(mb) * q, ws, s));
+    TRY(rowgemm<T>(basis, mb, nb, C + size_t(mb) * q, q, q, Wb, q, D, -1.0, 1.0, s));
+    return TRBL_OK;
+  }
+
+  // Cholesky QR twice: Vk = W R^{-1}, beta = R2 R1.  Returns the number of
+  // deficient columns found in pass 1 (their flags stay in hflags).
+  int cholqr2(T* Win, double thresh_abs, double thresh_rel, int* ndef) {
+    TRY(block_dot<T>(Win, q, q, Win, q, q, D, G, ws, s));
+    chol_kernel<<<1, 64, 0, s>>>(G, q, thresh_abs, thresh_rel, R1, R1i, flags + kF1);
+    TRBL_CUDA(cudaGetLastError());
+    TRBL_CUDA(cudaMemcpyAsync(hflags + kF1, flags + kF1, sizeof(int) * (q + 1), cudaMemcpyDeviceToHost, s));
+    TRY(rowgemm<T>(Win, q, q, R1i, q, q, W2, q, D, 1.0, 0.0, s));
+    TRY(block_dot<T>(W2, q, q, W2, q, q, D, G, ws, s));
+    chol_kernel<<<1, 64, 0, s>>>(G, q, 0.0, 1e-3, R2, R2i, flags + kF2);
+    TRBL_CUDA(cudaGetLastError());
+    TRBL_CUDA(cudaMemcpyAsync(hflags + kF2, flags + kF2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TRY(rowgemm<T>(W2, q, q, R2i, q, q, Vk, q, D, 1.0, 0.0, s));
+    upper_mul_kernel<<<(q * q + 127) / 128, 128, 0, s>>>(R2, R1, q, beta);
+    TRBL_CUDA(cudaGetLastError());
+    TRBL_CUDA(cudaStreamSynchronize(s));
+    *ndef = hflags[kF1] + hflags[kF2];
+    return TRBL_OK;
+  }
+
+  // QR of W (already orthogonal to the basis) with repair of deficient columns.
+  int block_qr(int nb) {
+    int ndef = 0;
+    TRY(cholqr2(W, tau * normH, 0.0, &ndef));
+    if (ndef == 0) return TRBL_OK;
+    // Keep W; replace the deficient columns by seeded random vectors,
+    // orthogonalise against the basis, QR again, and set beta = V_{k+1}^T W.
+    TRBL_CUDA(cudaMemcpyAsync(Wsave, W, sizeof(T) * D * q, cudaMemcpyDeviceToDevice, s));
+    std::vector<int> bad;
+    for (int j = 0; j < q; ++j)
+      if (hflags[kF1 + 1 + j] || hflags[kF2]) bad.push_back(j);
+    for (int j : bad) TRY(random_block<T>(W + j, q, D, 1, q, j, p->seed + 0x9e37ull * (++reseed), s));
+    TRY(cgs2(W, nb, nullptr));
+    TRY(cholqr2(W, 0.0, 1e-6, &ndef));
+    if (ndef) return fail(TRBL_ERR_BREAKDOWN, "block QR: block stays rank deficient after repair");
+    TRY(block_dot<T>(Vk, q, q, Wsave, q, q, D, beta, ws, s));
+    return TRBL_OK;
+  }
+
+  // Eigenpairs of T[0:nb, 0:nb]; copies theta[0:nev], theta[nb-1] and the
+  // residual estimates res[0:nev] to the host.
+  int ritz(int nb) {
+    TRBL_CUDA(cudaMemcpy2DAsync(Aw, sizeof(double) * mb, Tm, sizeof(double) * mb, sizeof(double) * nb, nb,
+                                cudaMemcpyDeviceToDevice, s));
+    TRBL_SOLVER(cusolverDnDsyevd(sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nb, Aw, mb, theta,
+                                 syev_work, lwork, devinfo));
+    const int n = std::min(nev, nb);
+    ritz_resid_kernel<<<(n + 127) / 128, 128, 0, s>>>(beta, q, Aw, mb, nb, n, res);
+    TRBL_CUDA(cudaGetLastError());
+    TRBL_CUDA(cudaMemcpyAsync(hbuf, theta, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+    TRBL_CUDA(cudaMemcpyAsync(hbuf + mb, res, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    TRBL_CUDA(cudaMemcpyAsync(hflags + kInfo, devinfo, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TRBL_CUDA(cudaStreamSynchronize(s));
+    if (hflags[kInfo] != 0) return fail(TRBL_ERR_CUDA, "syevd info=%d", hflags[kInfo]);
+    const double est = std::max(std::fabs(hbuf[0]), std::fabs(hbuf[nb - 1]));
+    if (p->normH <= 0.0) normH = std::max(normH, est);
+    return TRBL_OK;
+  }
+
+  // basis[:, 0:n_out] <- basis[:, 0:nb] U[:, 0:n_out] in row panels
+  int compress(int nb, int n_out) {
+    transpose_kernel<<<(nb * n_out + 255) / 256, 256, 0, s>>>(Aw, mb, nb, n_out, Ut);
+    TRBL_CUDA(cudaGetLastError());
+    for (int64_t r0 = 0; r0 < D; r0 += panel_rows) {
+      const int64_t nr = std::min(panel_rows, D - r0);
+      TRY(rowgemm<T>(basis + r0 * mb, mb, nb, Ut, n_out, n_out, panel, n_out, nr, 1.0, 0.0, s));
+      TRY(copy_cols<T, T>(panel, n_out, basis + r0 * mb, mb, nr, n_out, s));
+    }
+    return TRBL_OK;
+  }
+
+  // ---- stepping state ----
+  Timer tm;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  double ms_apply = 0, ms_orth = 0, ms_qr = 0, ms_ritz = 0, ms_restart = 0;
+  int nb = 0, iter = 0, restarts = 0, conv = 0;
+  bool done = false, have_ritz = false, finished = false;
+
+  // Start block: seeded random D x q, orthonormalised (Alg. 4, first line).
+  int init() {
+    TRY(tm.init(true));
+    TRBL_CUDA(cudaEventCreate(&t0));
+    TRBL_CUDA(cudaEventCreate(&t1));
+    TRBL_CUDA(cudaEventRecord(t0, s));
+    trace("init: D=%lld q=%d nev=%d max_basis=%d keep=%d", (long long)D, q, nev, mb, ls);
+    TRY(random_block<T>(W, q, D, q, q, 0, p->seed, s));
+    int ndef = 0;
+    TRY(cholqr2(W, 0.0, 1e-8, &ndef));
+    if (ndef) return fail(TRBL_ERR_BREAKDOWN, "start block is rank deficient (q > D?)");
+    TRY(copy_cols<T, T>(Vk, q, basis, mb, D, q, s));
+    nb = q;
+    return TRBL_OK;
+  }
+
+  // One block step of Alg. 4 (plus a thick restart when the basis is full).
+  int step(int* conv_out) {
+    if (conv_out) *conv_out = -1;
+    if (done) {
+      if (conv_out) *conv_out = conv;
+      return TRBL_OK;
+    }
+    const int check_every = p->check_every > 0 ? p->check_every : 1;
+    const int max_iter = p->max_iter > 0 ? p->max_iter : 100000;
+    trace("iter %d nb %d", iter, nb);
+    tm.rec(0, s);
+    TRY(apply(Vk, W));
+    tm.rec(1, s);
+    double* C1 = C + size_t(2) * mb * q;
+    TRY(cgs2(W, nb, C1));
+    set_alpha_kernel<<<(q * q + 127) / 128, 128, 0, s>>>(Tm, mb, C1, nb - q, q);
+    TRBL_CUDA(cudaGetLastError());
+    tm.rec(2, s);
+    TRY(block_qr(nb));
+    tm.rec(3, s);
+    ++iter;
+    const bool need_restart = nb + q > mb;
+    const bool check = need_restart || iter % check_every == 0 || iter >= max_iter;
+    have_ritz = false;
+    if (check) {
+      TRY(ritz(nb));
+      have_ritz = true;
+      const double lim = p->tol * normH;
+      conv = 0;
+      for (int i = 0; i < std::min(nev, nb); ++i)
+        if (hbuf[mb + i] <= lim) ++conv;
+      if (nb >= nev && conv == nev) done = true;
+      if (conv_out) *conv_out = conv;
+      trace("ritz: theta0 %.12g normH %.6g converged %d", hbuf[0], normH, conv);
+    }
+    tm.rec(4, s);
+    if (!done && iter < max_iter) {
+      if (need_restart) {
+        trace("restart nb %d -> %d", nb, ls + q);
+        TRY(compress(nb, ls));
+        TRBL_CUDA(cudaMemsetAsync(Tm, 0, sizeof(double) * mb * mb, s));
+        restart_t_kernel<<<(ls * q + 127) / 128, 128, 0, s>>>(Tm, mb, theta, beta, q, Aw, mb, nb, ls);
+        TRBL_CUDA(cudaGetLastError());
+        TRY(copy_cols<T, T>(Vk, q, basis + ls, mb, D, q, s));
+        nb = ls + q;
+        have_ritz = false;
+        ++restarts;
+      } else {
+        set_beta_kernel<<<(q * q + 127) / 128, 128, 0, s>>>(Tm, mb, beta, nb, nb - q, q);
+        TRBL_CUDA(cudaGetLastError());
+        TRY(copy_cols<T, T>(Vk, q, basis + nb, mb, D, q, s));
+        nb += q;
+        have_ritz = false;
+      }
+    }
+    tm.rec(5, s);
+    TRBL_CUDA(cudaEventSynchronize(tm.ev[5]));
+    ms_apply += tm.ms(0, 1);
+    ms_orth += tm.ms(1, 2);
+    ms_qr += tm.ms(2, 3);
+    ms_ritz += tm.ms(3, 4);
+    ms_restart += tm.ms(4, 5);
+    return TRBL_OK;
+  }
+
+  void fill_stats(trbl_stats* st, int status) {
+    st->iterations = iter;
+    st->restarts = restarts;
+    st->converged = conv;
+    st->status = status;
+    st->normH = normH;
+    st->ms_apply = ms_apply;
+    st->ms_orth = ms_orth;
+    st->ms_qr = ms_qr;
+    st->ms_ritz = ms_ritz;
+    st->ms_restart = ms_restart;
+  }
+
+  // Ritz values, vectors and true residuals of the current basis.
+  int finish(double* evals, double* resid, void* evecs, trbl_stats* st) {
+    const int status = done ? TRBL_OK : TRBL_ERR_NOCONV;
+    trace("finish: status %d", status);
+    // After an append or a restart the basis holds one more block than T's
+    // last Rayleigh-Ritz step saw; the Ritz pairs below use the block
+    // diagonal part of T that is complete (rows 0 .. nb - q).
+    int nr = have_ritz ? nb : nb - q;
+    if (!have_ritz) TRY(ritz(nr));
+    const int n = std::min(nev, nr);
+    for (int i = 0; i < n; ++i) evals[i] = hbuf[i];
+    for (int i = n; i < nev; ++i) evals[i] = NAN;
+    transpose_kernel<<<(nr * n + 255) / 256, 256, 0, s>>>(Aw, mb, nr, n, Ut);
+    TRBL_CUDA(cudaGetLastError());
+    if (evecs) TRY(rowgemm<T>(basis, mb, nr, Ut, n, n, static_cast<T*>(evecs), nev, D, 1.0, 0.0, s));
+    if (resid) {
+      // true residuals ||H x - theta x|| with an FP64 apply, q columns at a time
+      const int64_t nchunk = nchunk_res;
+      const int64_t rows = (D + nchunk - 1) / nchunk;
+      for (int c0 = 0; c0 < n; c0 += q) {
+        const int nc = std::min(q, n - c0);
+        if constexpr (std::is_same<T, double>::value) {
+          TRY(rowgemm<double>(basis, mb, nr, Ut + c0, n, nc, Xd, nc, D, 1.0, 0.0, s));
+        } else {
+          TRY(rowgemm<T>(basis, mb, nr, Ut + c0, n, nc, W, nc, D, 1.0, 0.0, s));
+          TRY(copy_cols<T, double>(W, nc, Xd, nc, D, nc, s));
+        }
+        TRY(launch_apply(h, Xd, nc, HXd, nc, nc, TRBL_F64, s));
+        resid_partial_kernel<<<unsigned(nchunk), 64, 0, s>>>(HXd, Xd, nc, theta + c0, D, rows, rpart);
+        TRBL_CUDA(cudaGetLastError());
+        resid_final_kernel<<<1, 64, 0, s>>>(rpart, int(nchunk), nc, rtrue + c0);
+        TRBL_CUDA(cudaGetLastError());
+      }
+      TRBL_CUDA(cudaMemcpyAsync(resid, rtrue, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    }
+    TRBL_CUDA(cudaEventRecord(t1, s));
+    TRBL_CUDA(cudaStreamSynchronize(s));
+    if (resid)
+      for (int i = n; i < nev; ++i) resid[i] = NAN;
+    if (st) {
+      fill_stats(st, status);
+      float tot = 0.f;
+      cudaEventElapsedTime(&tot, t0, t1);
+      st->ms_total = tot;
+    }
+    finished = true;
+    if (status == TRBL_ERR_NOCONV)
+      return fail(TRBL_ERR_NOCONV, "not converged after %d block iterations (%d of %d pairs)", iter, conv, nev);
+    return TRBL_OK;
+  }
+
+  int setup() {
+    const trbl_basis* b = h->b;
+    D = b->D;
+    q = p->q;
+    nev = p->nev;
+    mb = p->max_basis;
+    dtype = std::is_same<T, double>::value ? TRBL_F64 : TRBL_F32;
+    tau = dtype == TRBL_F64 ? 1e-10 : 1e-4;
+    if (q < 1 || q > 64) return fail(TRBL_ERR_ARG, "q=%d outside [1, 64]", q);
+    if (nev < 1) return fail(TRBL_ERR_ARG, "nev must be positive");
+    if (mb > D) return fail(TRBL_ERR_ARG, "max_basis=%d exceeds the dimension %lld", mb, (long long)D);
+    if (mb < nev + 2 * q) return fail(TRBL_ERR_ARG, "max_basis must be at least nev + 2q");
+    if (!(p->tol > 0.0)) return fail(TRBL_ERR_ARG, "tol must be positive");
+    ls = p->keep;
+    if (ls <= 0) ls = nev + (mb - nev) / 4;
+    ls = std::min(ls, mb - 2 * q);
+    if (ls < nev) return fail(TRBL_ERR_ARG, "keep=%d smaller than nev=%d", ls, nev);
+    normH = p->normH > 0.0 ? p->normH : 0.0;
+    int dev = 0;
+    TRBL_CUDA(cudaGetDevice(&dev));
+    TRBL_CUDA(cudaDeviceGetAttribute(&ws.sm_count, cudaDevAttrMultiProcessorCount, dev));
+    panel_rows = std::max<int64_t>(4096, (int64_t(1) << 30) / (int64_t(ls) * sizeof(T)));
+    panel_rows = std::min(panel_rows, D);
+    const size_t dq = size_t(D) * q;
+    ws.partial_bytes = block_dot_workspace_bytes(q, q, ws.sm_count);
+    for (int m = 1; m <= mb; ++m)
+      ws.partial_bytes = std::max(ws.partial_bytes, block_dot_workspace_bytes(m, q, ws.sm_count));
+    nchunk_res = std::min<int64_t>(4 * ws.sm_count, (D + 1023) / 1024);
+    // Two passes over the same sequence of takes: size, then carve.
+    for (int pass = 0; pass < 2; ++pass) {
+      ar.off = 0;
+      basis = ar.take<T>(size_t(D) * mb);
+      Vk = ar.take<T>(dq);
+      W = ar.take<T>(dq);
+      W2 = ar.take<T>(dq);
+      Wsave = ar.take<T>(dq);
+      panel = ar.take<T>(size_t(panel_rows) * ls);
+      C = ar.take<double>(size_t(3) * mb * q);
+      G = ar.take<double>(q * q);
+      R1 = ar.take<double>(q * q);
+      R1i = ar.take<double>(q * q);
+      R2 = ar.take<double>(q * q);
+      R2i = ar.take<double>(q * q);
+      beta = ar.take<double>(q * q);
+      Tm = ar.take<double>(size_t(mb) * mb);
+      Aw = ar.take<double>(size_t(mb) * mb);
+      Ut = ar.take<double>(size_t(mb) * mb);
+      theta = ar.take<double>(mb);
+      res = ar.take<double>(mb);
+      Xd = ar.take<double>(dq);
+      HXd = ar.take<double>(dq);
+      rpart = ar.take<double>(size_t(nchunk_res) * q);
+      rtrue = ar.take<double>(mb);
+      ws.partial = ar.take<double>(ws.partial_bytes / sizeof(double));
+      flags = ar.take<int>(kFlagInts);
+      if (pass == 0) {
+        const size_t bytes = ar.off;
+        cudaError_t e = cudaMalloc(&ar.base, bytes);
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          ar.base = nullptr;
+          return fail(TRBL_ERR_OOM, "solver workspace of %.2f GB: %s", bytes / 1e9, cudaGetErrorString(e));
+        }
+        ar.cap = bytes;
+      }
+    }
+    devinfo = flags + kInfo;
+    trace("workspace %.3f GB at %p", ar.cap / 1e9, ar.base);
+    if (cusolverDnCreate(&sol) != CUSOLVER_STATUS_SUCCESS) return fail(TRBL_ERR_CUDA, "cusolverDnCreate failed");
+    TRBL_SOLVER(cusolverDnSetStream(sol, s));
+    TRBL_SOLVER(cusolverDnDsyevd_bufferSize(sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, mb, Aw, mb,
+                                            theta, &lwork));
+    trace("syevd lwork %d", lwork);
+    {
+      cudaError_t e = cudaMalloc(&syev_work, sizeof(double) * size_t(std::max(lwork, 1)));
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        syev_work = nullptr;
+        return fail(TRBL_ERR_OOM, "syevd workspace: %s", cudaGetErrorString(e));
+      }
+    }
+    TRBL_CUDA(cudaMemsetAsync(Tm, 0, sizeof(double) * mb * mb, s));
+    TRBL_CUDA(cudaMallocHost(&hbuf, sizeof(double) * (2 * mb) + sizeof(int) * kFlagInts));
+    hflags = reinterpret_cast<int*>(hbuf + 2 * mb);
+    return TRBL_OK;
+  }
+};
+
+
+// Type-erased solver behind the C ABI.
+struct SolverBase {
+  virtual ~SolverBase() {}
+  virtual int init() = 0;
+  virtual int step(int* conv) = 0;
+  virtual int finish(double* evals, double* resid, void* evecs, trbl_stats* st) = 0;
+  virtual void stats(trbl_stats* st) = 0;
+  virtual void* block() = 0;
+  virtual size_t block_bytes() = 0;
+  virtual bool is_done() = 0;
+  virtual int iterations() = 0;
+};
+
+template <typename T>
+struct SolverImpl : SolverBase {
+  Solver<T> S{};
+  int init() override { return S.init(); }
+  int step(int* c) override { return S.step(c); }
+  int finish(double* e, double* r, void* v, trbl_stats* st) override { return S.finish(e, r, v, st); }
+  void stats(trbl_stats* st) override {
+    S.fill_stats(st, TRBL_OK);
+    float tot = 0.f;
+    cudaEventRecord(S.t1, S.s);
+    cudaEventSynchronize(S.t1);
+    cudaEventElapsedTime(&tot, S.t0, S.t1);
+    st->ms_total = tot;
+  }
+  void* block() override { return S.Vk; }
+  size_t block_bytes() override { return sizeof(T) * size_t(S.D) * S.q; }
+  bool is_done() override { return S.done; }
+  int iterations() override { return S.iter; }
+};
+
+}  // namespace
+}  // namespace trbl
+
+struct trbl_solver {
+  trbl_params params;
+  cudaStream_t stream = nullptr;
+  trbl::SolverBase* impl = nullptr;
+  ~trbl_solver() { delete impl; }
+};
+
+using namespace trbl;
+
+extern "C" int trbl_solver_create(const trbl_hamiltonian* h, const trbl_params* p, void* stream,
+                                  trbl_solver** out) {
+  clear_error();
+  if (!out) return fail(TRBL_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (!h || !p) return fail(TRBL_ERR_ARG, "null argument");
+  trbl_solver* sv = new (std::nothrow) trbl_solver();
+  if (!sv) return fail(TRBL_ERR_OOM, "host allocation failed");
+  sv->params = *p;
+  sv->stream = static_cast<cudaStream_t>(stream);
+  int rc = TRBL_OK;
+  auto make = [&](auto* impl) {
+    if (!impl) {
+      rc = fail(TRBL_ERR_OOM, "host allocation failed");
+      return;
+    }
+    impl->S.h = h;
+    impl->S.p = &sv->params;
+    impl->S.s = sv->stream;
+    sv->impl = impl;
+    rc = impl->S.setup();
+    if (rc == TRBL_OK) rc = impl->init();
+  };
+  if (p->precision == TRBL_PREC_F64)
+    make(new (std::nothrow) SolverImpl<double>());
+  else if (p->precision == TRBL_PREC_MIXED)
+    make(new (std::nothrow) SolverImpl<float>());
+  else
+    rc = fail(TRBL_ERR_ARG, "precision must be TRBL_PREC_F64 or TRBL_PREC_MIXED");
+  if (rc != TRBL_OK) {
+    delete sv;
+    return rc;
+  }
+  *out = sv;
+  return TRBL_OK;
+}
+
+extern "C" int trbl_solver_step(trbl_solver* sv, int* converged) {
+  clear_error();
+  if (!sv || !sv->impl) return fail(TRBL_ERR_ARG, "null solver");
+  return sv->impl->step(converged);
+}
+
+extern "C" int trbl_solver_step_host(trbl_solver* sv, const void* block_in, void* block_out, int* converged) {
+  clear_error();
+  if (!sv || !sv->impl) return fail(TRBL_ERR_ARG, "null solver");
+  const size_t bytes = sv->impl->block_bytes();
+  if (block_in)
+    TRBL_CUDA(cudaMemcpyAsync(sv->impl->block(), block_in, bytes, cudaMemcpyHostToDevice, sv->stream));
+  int rc = sv->impl->step(converged);
+  if (rc) return rc;
+  if (block_out) {
+    TRBL_CUDA(cudaMemcpyAsync(block_out, sv->impl->block(), bytes, cudaMemcpyDeviceToHost, sv->stream));
+    TRBL_CUDA(cudaStreamSynchronize(sv->stream));
+  }
+  return TRBL_OK;
+}
+
+extern "C" int trbl_solver_block(trbl_solver* sv, void** block, int64_t* bytes) {
+  clear_error();
+  if (!sv || !sv->impl) return fail(TRBL_ERR_ARG, "null solver");
+  if (block) *block = sv->impl->block();
+  if (bytes) *bytes = int64_t(sv->impl->block_bytes());
+  return TRBL_OK;
+}
+
+extern "C" int trbl_solver_stats(trbl_solver* sv, trbl_stats* st) {
+  clear_error();
+  if (!sv || !sv->impl || !st) return fail(TRBL_ERR_ARG, "null argument");
+  *st = trbl_stats{};
+  sv->impl->stats(st);
+  return TRBL_OK;
+}
+
+extern "C" int trbl_solver_finish(trbl_solver* sv, double* evals, double* resid, void* evecs,
+                                  trbl_stats* stats) {
+  clear_error();
+  if (!sv || !sv->impl || !evals) return fail(TRBL_ERR_ARG, "null argument");
+  if (stats) *stats = trbl_stats{};
+  int rc = sv->impl->finish(evals, resid, evecs, stats);
+  if (stats) stats->status = rc;
+  return rc;
+}
+
+extern "C" void trbl_solver_destroy(trbl_solver* sv) {
+  if (!sv) return;
+  if (sv->stream) cudaStreamSynchronize(sv->stream);
+  delete sv;
+}
+
+extern "C" int trbl_solve(const trbl_hamiltonian* h, const trbl_params* p, double* evals, double* resid,
+                          void* evecs, trbl_stats* stats, void* stream) {
+  clear_error();
+  if (!h || !p || !evals) return fail(TRBL_ERR_ARG, "null argument");
+  if (stats) *stats = trbl_stats{};
+  trbl_solver* sv = nullptr;
+  int rc = trbl_solver_create(h, p, stream, &sv);
+  if (rc != TRBL_OK) {
+    if (stats) stats->status = rc;
+    return rc;
+  }
+  const int max_iter = p->max_iter > 0 ? p->max_iter : 100000;
+  while (rc == TRBL_OK && !sv->impl->is_done() && sv->impl->iterations() < max_iter) rc = sv->impl->step(nullptr);
+  if (rc == TRBL_OK) rc = trbl_solver_finish(sv, evals, resid, evecs, stats);
+  std::string keep = trbl_last_error();
+  trbl_solver_destroy(sv);
+  if (rc != TRBL_OK) fail(rc, "%s", keep.c_str());
+  if (stats) stats->status = rc;
+  return rc;
+}

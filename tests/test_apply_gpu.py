@@ -1,0 +1,165 @@
+"""Parity of the CUDA block product W = H V (App. B) with the oracle.
+
+Small spaces: every element of W against the oracle's explicit CSR H times
+the same V.  Full 20-m-state spaces: sampled rows (block edges, first/last
+row, random rows) against the oracle's one-row-at-a-time product.
+
+Tolerance (elementwise, derived from recursive-summation error bounds):
+|W - H V|_ij <= rtol * (|H| |V|)_ij with rtol = 1e-12 in FP64 and 1e-5 in
+FP32 (coefficients rounded to FP32 once; V is rounded to FP32 before the
+oracle sees it, so input rounding is not counted).
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import basis as ob
+from oracle import hamiltonian as oh
+
+torch = pytest.importorskip("torch")
+trbl = pytest.importorskip("paper_1902_02064_gb300")
+
+pytestmark = pytest.mark.gpu
+
+RTOL = {torch.float64: 1e-12, torch.float32: 1e-5}
+
+
+def _setup(name):
+    w, sa, sb, inter = synth.workload(name)
+    B = ob.ProductBasis(sa.twom, w.nA, sb.twom, w.nB, w.twoM)
+    H = oh.assemble(B, inter)
+    tb = trbl.Basis(sa, w.nA, sb, w.nB, w.twoM)
+    th = trbl.Hamiltonian.from_interaction(tb, inter)
+    return w, B, H, tb, th
+
+
+@pytest.fixture(scope="module")
+def small():
+    return _setup("s12_2p2n")
+
+
+@pytest.fixture(scope="module")
+def medium():
+    return _setup("s12_4p4n")
+
+
+def _check(W, H, V, dtype):
+    Vd = V.astype(np.float64)
+    ref = H @ Vd
+    bound = abs(H) @ np.abs(Vd)
+    err = np.abs(W.astype(np.float64) - ref)
+    assert np.all(err <= RTOL[dtype] * bound + 1e-300), float((err / (bound + 1e-300)).max())
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("q", [1, 3, 4, 8, 16, 32, 64])
+def test_apply_small_all_elements(small, dtype, q):
+    w, B, H, tb, th = small
+    V = torch.from_numpy(synth.random_block(B.dim, q, 10 + q)).to(dtype)
+    W = th.apply(V.cuda())
+    torch.cuda.synchronize()
+    _check(W.cpu().numpy(), H, V.numpy(), dtype)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("q", [8, 16])
+def test_apply_medium_all_elements(medium, dtype, q):
+    w, B, H, tb, th = medium
+    V = torch.from_numpy(synth.random_block(B.dim, q, 20 + q)).to(dtype)
+    W = th.apply(V.cuda())
+    torch.cuda.synchronize()
+    _check(W.cpu().numpy(), H, V.numpy(), dtype)
+
+
+def test_apply_strided_leading_dimension(small):
+    w, B, H, tb, th = small
+    q, ld = 4, 11
+    big = torch.from_numpy(synth.random_block(B.dim, ld, 3)).cuda()
+    V = big[:, 2:2 + q]
+    Wbig = torch.full((B.dim, 9), 7.0, dtype=torch.float64, device="cuda")
+    W = Wbig[:, 1:1 + q]
+    th.apply(V, W)
+    torch.cuda.synchronize()
+    _check(W.cpu().numpy(), H, V.cpu().numpy(), torch.float64)
+    assert torch.all(Wbig[:, 0] == 7.0) and torch.all(Wbig[:, 1 + q:] == 7.0)
+
+
+def test_apply_columns_independent(medium):
+    """Column j of H [V] equals H applied to column j alone (q = 1)."""
+    w, B, H, tb, th = medium
+    V = torch.from_numpy(synth.random_block(B.dim, 32, 5)).cuda()
+    W = th.apply(V)
+    for j in (0, 13, 31):
+        Wj = th.apply(V[:, j:j + 1].contiguous())
+        assert torch.allclose(W[:, j:j + 1], Wj, rtol=0, atol=1e-12 * W.abs().max().item())
+
+
+@pytest.mark.parametrize("kA,kB,twoM", [(0, 2, 0), (1, 1, 2), (3, 1, -2), (2, 3, 3)])
+def test_apply_edge_particle_numbers(kA, kB, twoM):
+    sp = synth.make_space(synth.SPACE12_SHELLS)
+    inter = synth.draw_interaction(sp, sp, 31)
+    B = ob.ProductBasis(sp.twom, kA, sp.twom, kB, twoM)
+    H = oh.assemble(B, inter)
+    tb = trbl.Basis(sp, kA, sp, kB, twoM)
+    th = trbl.Hamiltonian.from_interaction(tb, inter)
+    V = torch.from_numpy(synth.random_block(B.dim, 5, 1))
+    W = th.apply(V.cuda())
+    torch.cuda.synchronize()
+    _check(W.cpu().numpy(), H, V.numpy(), torch.float64)
+
+
+def test_apply_rejects_bad_arguments(small):
+    w, B, H, tb, th = small
+    V = torch.zeros((B.dim, 4), dtype=torch.float64, device="cuda")
+    with pytest.raises(trbl.TrblError):
+        trbl.trbl_apply_block(th.handle, V.data_ptr(), 4, V.data_ptr(), 4, 4, trbl.TRBL_F64, 0)
+    with pytest.raises(trbl.TrblError):
+        trbl.trbl_apply_block(th.handle, V.data_ptr(), 2, V.data_ptr(), 4, 4, trbl.TRBL_F64, 0)
+    host = np.zeros((B.dim, 4))
+    W = torch.zeros_like(V)
+    with pytest.raises(trbl.TrblError):
+        trbl.trbl_apply_block(th.handle, host.ctypes.data, 4, W.data_ptr(), 4, 4, trbl.TRBL_F64, 0)
+
+
+def _sample_rows(L, n_rand, seed):
+    rows = {0, L.dim - 1}
+    for (_, _, off, na, nb, _, _) in L.blocks:
+        rows.add(off)
+        rows.add(off + na * nb - 1)
+    rng = np.random.default_rng(seed)
+    rows.update(rng.integers(0, L.dim, n_rand).tolist())
+    return sorted(rows)
+
+
+@pytest.mark.parametrize("name,q,dtype", [("s20_4p4n", 16, torch.float64),
+                                          ("s20_4p4n", 16, torch.float32),
+                                          ("s20_5p5n", 32, torch.float32)])
+def test_apply_full_size_sampled_rows(name, q, dtype):
+    w, sa, sb, inter = synth.workload(name)
+    L = oh.LazyIndex(sa.twom, w.nA, sb.twom, w.nB, w.twoM)
+    T = oh.TermTables(inter)
+    tb = trbl.Basis(sa, w.nA, sb, w.nB, w.twoM)
+    assert tb.dim == L.dim
+    th = trbl.Hamiltonian.from_interaction(tb, inter)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(w.seed)
+    V = torch.rand((tb.dim, q), generator=g, device="cuda", dtype=dtype) * 2 - 1
+    W = th.apply(V)
+    torch.cuda.synchronize()
+    rows = _sample_rows(L, 24, w.seed)
+    Wr = W[torch.tensor(rows, device="cuda")].double().cpu().numpy()
+    for k, r in enumerate(rows):
+        SA, SB = L.state(r)
+        terms = oh.column_terms(SA, SB, T)
+        idx = torch.tensor([L.index(A2, B2) for _, A2, B2 in terms], device="cuda")
+        Vs = V[idx].double().cpu().numpy()
+        coef = np.array([v for v, _, _ in terms])
+        ref = coef @ Vs
+        bound = np.abs(coef) @ np.abs(Vs)
+        assert np.all(np.abs(Wr[k] - ref) <= RTOL[dtype] * bound), (r, np.abs(Wr[k] - ref).max())
+    # symmetry of H at full size: <x, H y> = <H x, y>
+    x = V[:, :1].double().contiguous()
+    y = V[:, 1:2].double().contiguous()
+    Hx, Hy = th.apply(x), th.apply(y)
+    a, b = torch.dot(x[:, 0], Hy[:, 0]).item(), torch.dot(Hx[:, 0], y[:, 0]).item()
+    assert abs(a - b) <= 1e-10 * (abs(a) + abs(b))

@@ -1,0 +1,136 @@
+"""Parity of the GPU thick-restart block Lanczos solver (Sec. III D, Alg. 4)
+with the oracle's eigenvalues.
+
+Bars: FP64 mode |theta_i - lambda_i| <= 1e-9 ||H||; mixed mode (FP32
+vectors and apply, FP64 coefficients, QR and Ritz) <= 1e-6 ||H||.
+Eigenvalues are compared as sorted lists; eigenvectors by the angle between
+the computed and exact eigenspaces of each cluster.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import basis as ob
+from oracle import hamiltonian as oh
+
+torch = pytest.importorskip("torch")
+trbl = pytest.importorskip("paper_1902_02064_gb300")
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def small():
+    w, sa, sb, inter = synth.workload("s12_2p2n")
+    B = ob.ProductBasis(sa.twom, w.nA, sb.twom, w.nB, w.twoM)
+    H = oh.assemble(B, inter)
+    ev, U = np.linalg.eigh(H.toarray())
+    tb = trbl.Basis(sa, w.nA, sb, w.nB, w.twoM)
+    th = trbl.Hamiltonian.from_interaction(tb, inter)
+    return w, H, ev, U, th
+
+
+@pytest.fixture(scope="module")
+def medium():
+    w, sa, sb, inter = synth.workload("s12_4p4n")
+    gold = json.load(open(os.path.join(GOLDEN, "eigs_s12_4p4n.json")))
+    tb = trbl.Basis(sa, w.nA, sb, w.nB, w.twoM)
+    th = trbl.Hamiltonian.from_interaction(tb, inter)
+    return w, gold, th
+
+
+def _subspace_ok(X, U, ev, nev, gap, tol):
+    """Every computed vector lies in the exact eigenspace of its cluster."""
+    i = 0
+    while i < nev:
+        j = i
+        while j + 1 < len(ev) and ev[j + 1] - ev[j] < gap:
+            j += 1
+        if j >= nev:  # cluster cut by nev: skip (not uniquely defined)
+            break
+        P = U[:, i:j + 1]
+        Xc = X[:, i:j + 1]
+        res = Xc - P @ (P.T @ Xc)
+        assert np.linalg.norm(res, axis=0).max() <= tol, (i, j)
+        i = j + 1
+
+
+def test_solve_small_fp64(small):
+    w, H, ev, U, th = small
+    normH = max(abs(ev[0]), abs(ev[-1]))
+    evals, resid, X, st = trbl.solve(th, w.nev, w.q, w.max_basis, w.tol, precision=trbl.TRBL_PREC_F64)
+    assert np.abs(evals - ev[: w.nev]).max() <= 1e-9 * normH
+    assert resid.max() <= 1e-8 * normH
+    Xh = X.cpu().numpy()
+    assert np.abs(Xh.T @ Xh - np.eye(w.nev)).max() < 1e-10
+    _subspace_ok(Xh, U, ev, w.nev, 1e-8 * normH, 1e-7)
+    assert st["restarts"] >= 1 and st["iterations"] > 0
+
+
+def test_solve_small_mixed(small):
+    w, H, ev, U, th = small
+    normH = max(abs(ev[0]), abs(ev[-1]))
+    evals, resid, X, st = trbl.solve(th, w.nev, w.q, w.max_basis, 1e-6, precision=trbl.TRBL_PREC_MIXED)
+    assert X.dtype == torch.float32
+    assert np.abs(evals - ev[: w.nev]).max() <= 1e-6 * normH
+    assert resid.max() <= 1e-4 * normH
+
+
+@pytest.mark.parametrize("q", [1, 2, 8])
+def test_solve_small_block_sizes(small, q):
+    w, H, ev, U, th = small
+    normH = max(abs(ev[0]), abs(ev[-1]))
+    evals, resid, X, st = trbl.solve(th, w.nev, q, 48, 1e-10, precision=trbl.TRBL_PREC_F64, keep=20)
+    assert np.abs(evals - ev[: w.nev]).max() <= 1e-9 * normH
+
+
+def test_solve_medium_fp64(medium):
+    w, gold, th = medium
+    normH = gold["normH"]
+    evals, resid, X, st = trbl.solve(th, w.nev, w.q, w.max_basis, w.tol, precision=trbl.TRBL_PREC_F64,
+                                     want_vectors=False)
+    ref = np.array(gold["evals"][: w.nev])
+    assert np.abs(evals - ref).max() <= 1e-9 * normH, np.abs(evals - ref).max()
+    assert resid.max() <= 1e-8 * normH
+
+
+def test_solve_medium_mixed(medium):
+    w, gold, th = medium
+    normH = gold["normH"]
+    evals, resid, X, st = trbl.solve(th, w.nev, w.q, w.max_basis, 1e-6, precision=trbl.TRBL_PREC_MIXED,
+                                     want_vectors=False)
+    ref = np.array(gold["evals"][: w.nev])
+    err = np.abs(evals - ref).max()
+    assert err <= 1e-6 * normH, err
+
+
+def test_solve_degenerate_spectrum_repairs_block():
+    """One-body-only H: highly degenerate levels and an invariant Krylov
+    subspace, so the block QR must replace exhausted directions."""
+    sp = synth.make_space(synth.SPACE12_SHELLS)
+    inter = synth.draw_interaction(sp, sp, 0)
+    for a in (inter.VAA, inter.VBB, inter.VAB):
+        a[...] = 0.0
+    B = ob.ProductBasis(sp.twom, 2, sp.twom, 2, 0)
+    ev = np.linalg.eigvalsh(oh.assemble(B, inter).toarray())
+    tb = trbl.Basis(sp, 2, sp, 2, 0)
+    th = trbl.Hamiltonian.from_interaction(tb, inter)
+    evals, resid, X, st = trbl.solve(th, 6, 4, 40, 1e-10, precision=trbl.TRBL_PREC_F64, normH=ev[-1],
+                                     max_iter=2000)
+    assert np.abs(evals - ev[:6]).max() <= 1e-9 * ev[-1]
+
+
+def test_solve_reports_noconv_and_bad_args(small):
+    w, H, ev, U, th = small
+    evals, resid, X, st = trbl.solve(th, w.nev, w.q, w.max_basis, 1e-14, max_iter=4,
+                                     raise_on_noconv=False)
+    assert st["rc"] == trbl.TRBL_ERR_NOCONV and np.all(np.isfinite(evals))
+    with pytest.raises(trbl.TrblError) as e:
+        trbl.solve(th, w.nev, w.q, 10_000, w.tol)
+    assert e.value.code == trbl.TRBL_ERR_ARG
+    with pytest.raises(trbl.TrblError):
+        trbl.solve(th, 30, 8, 40, w.tol)  # max_basis < nev + 2q
