@@ -1,0 +1,446 @@
+"""Benchmark: thick-restart block Lanczos steps on the 20-m-state 5+5 M-scheme
+space (D = 18,600,516), block size q = 32, mixed precision (FP32 vectors
+and on-the-fly block product, FP64 projection coefficients, Cholesky QR and
+Rayleigh-Ritz), basis of up to 1024 vectors.
+
+One step = one block iteration of the solver: W = H V_k (matrix elements
+generated on the fly), full reorthogonalisation against the stored basis
+(classical Gram-Schmidt twice), Cholesky QR twice, Rayleigh-Ritz on the
+projected matrix, and a thick restart when the basis is full.  The
+Hamiltonian's tables are built once before timing.
+
+metric: block H.V throughput, GNZ*q/s = structural nonzeros of H * q per
+second of step time (nonzeros counted before cancellation: pairs of basis
+states linked by any M-allowed term).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): every rank solves its own independent replica
+(replicas only; no data-path collective); value = all ranks' work / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+WORKLOAD = "s20_5p5n"
+METRIC = "block H·V GNZ·q/s"
+UNIT = "GNZ*q/s"
+
+
+def popcount32(x: np.ndarray) -> np.ndarray:
+    x = x.astype(np.uint32)
+    if hasattr(np, "bitwise_count"):
+        return np.bitwise_count(x).astype(np.int64)
+    x = x - ((x >> 1) & 0x55555555)
+    x = (x & 0x33333333) + ((x >> 2) & 0x33333333)
+    return ((((x + (x >> 4)) & 0x0F0F0F0F) * 0x01010101) & 0xFFFFFFFF) >> 24
+
+
+def slab_rows(bitsA, mA, mB, twoM) -> int:
+    """R = sum over target A determinants p' of sum over the distinct source
+    A determinants p feeding it (like-particle terms: same 2M, at most two
+    particles moved; one-body jumps of the factorised cross term: one
+    particle moved, any 2M) of N_B(2M - 2M_p): the neutron-slab rows one
+    apply must read in the factorised slab model."""
+    nbB = {}
+    for m in mB:
+        nbB[int(m)] = nbB.get(int(m), 0) + 1
+    NBp = np.array([nbB.get(twoM - int(m), 0) for m in mA], dtype=np.int64)
+    R = 0
+    for i in range(len(bitsA)):
+        if NBp[i] == 0:
+            continue
+        pc = popcount32(bitsA ^ bitsA[i])
+        src = (pc <= 2) | ((pc <= 4) & (mA == mA[i]))
+        R += int(NBp[src].sum())
+    return R
+
+
+def structural_nnz(bitsA, mA, bitsB, mB, blocks) -> int:
+    """Pairs (i, j) of basis states linked by an M-allowed term of H: the
+    A and B parts together move at most two particles, total 2M equal.
+    Counted per (A pair, B pair) class with the block sizes."""
+    # For each A determinant p and each A source p (any 2M), the number of
+    # moved particles dA; likewise for B.  A pair of product states is
+    # linked iff dA + dB <= 2 and both lie in the basis.
+    from collections import defaultdict
+    idxB = defaultdict(list)
+    for j, m in enumerate(mB):
+        idxB[int(m)].append(j)
+    # count B pairs by (M_B target, M_B source, dB)
+    cntB = defaultdict(int)
+    for mt, js in idxB.items():
+        bt = bitsB[js]
+        for ms, ks in idxB.items():
+            bs = bitsB[ks]
+            for x in bt:
+                pc = popcount32(bs ^ x) // 2
+                for d in (0, 1, 2):
+                    c = int(np.count_nonzero(pc == d))
+                    if c:
+                        cntB[(mt, ms, d)] += c
+    twoM = int(blocks[0][0] + blocks[0][1])
+    total = 0
+    mA_set = sorted(set(int(m) for m in mA))
+    idxA = {m: np.nonzero(mA == m)[0] for m in mA_set}
+    for mt in mA_set:
+        at = bitsA[idxA[mt]]
+        for ms in mA_set:
+            as_ = bitsA[idxA[ms]]
+            for x in at:
+                pc = popcount32(as_ ^ x) // 2
+                for d in (0, 1, 2):
+                    c = int(np.count_nonzero(pc == d))
+                    if not c:
+                        continue
+                    for dB in range(0, 3 - d):
+                        total += c * cntB.get((twoM - mt, twoM - ms, dB), 0)
+    return total
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def ncu_traffic(path=os.path.join(ROOT, "profiles", "apply_traffic.json")):
+    """DRAM bytes per apply launch from a committed ncu summary, if current."""
+    try:
+        d = json.load(open(path))
+        return d.get("dram_bytes_per_launch_full_size")
+    except (OSError, ValueError):
+        return None
+
+
+# ----------------------------------------------------------------------------
+# oracle timing (reference arm and cpu_baseline)
+# ----------------------------------------------------------------------------
+
+class _RowGen:
+    """Rows of a seeded uniform(-1, 1) D x q block, generated on demand."""
+
+    def __init__(self, q, seed):
+        self.q, self.seed = q, seed
+
+    def __getitem__(self, i):
+        idx = np.arange(self.q, dtype=np.uint64) + np.uint64(int(i) * self.q) \
+            + np.uint64((self.seed & 0xFFFFFFFF) << 32)
+        h = synth.splitmix64(idx)
+        return ((h >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))) * 2.0 - 1.0
+
+
+class OracleSample:
+    """The oracle's one-row-at-a-time H.V on a sample of rows of the workload."""
+
+    def __init__(self, name, q):
+        from oracle import hamiltonian as oh
+        self.oh = oh
+        w, sa, sb, inter = synth.workload(name)
+        self.L = oh.LazyIndex(sa.twom, w.nA, sb.twom, w.nB, w.twoM)
+        self.T = oh.TermTables(inter)
+        self.V = _RowGen(q, w.seed)
+        self.q = q
+        self.rng = np.random.default_rng(1234)
+
+    def run(self, seconds):
+        """Rows until `seconds` pass; returns (structural nnz * q, elapsed)."""
+        t0 = time.perf_counter()
+        work = 0
+        rows = 0
+        while time.perf_counter() - t0 < seconds:
+            r = int(self.rng.integers(0, self.L.dim))
+            SA, SB = self.L.state(r)
+            targets = set()
+            acc = np.zeros(self.q)
+            for v, A2, B2 in self.oh.column_terms(SA, SB, self.T):
+                j = self.L.index(A2, B2)
+                acc += v * self.V[j]
+                targets.add(j)
+            work += len(targets) * self.q
+            rows += 1
+        return work, time.perf_counter() - t0, rows
+
+
+def cpu_baseline(name, q, seconds):
+    o = OracleSample(name, q)
+    work, el, rows = o.run(seconds)
+    return {"value": work / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d random rows of H.V (q=%d) of the %s workload by the FP64 oracle's "
+                      "one-row-at-a-time operator application, %.1f s" % (rows, q, name, el)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = synth.WORKLOADS[WORKLOAD]
+    o = OracleSample(WORKLOAD, w.q)
+    per_step = 3.0
+    for _ in range(args.warmup):
+        o.run(per_step / 3)
+    works, times, rows = 0, 0.0, 0
+    for _ in range(args.steps):
+        wk, el, rw = o.run(per_step)
+        works += wk
+        times += el
+        rows += rw
+    value = works / times / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": times / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "q": w.q, "dim": 18600516},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d random rows of H.V per %d steps, FP64 oracle, one core" % (rows, args.steps)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_1902_02064_gb300 as trbl
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w, sa, sb, inter = synth.workload(WORKLOAD)
+    q = w.q
+    tb = trbl.Basis(sa, w.nA, sb, w.nB, w.twoM)
+    th = trbl.Hamiltonian.from_interaction(tb, inter)
+    D = tb.dim
+    bitsA, mA, bitsB, mB, blocks = tb.export()
+    R = slab_rows(bitsA, mA, mB, w.twoM)
+    nnz = structural_nnz(bitsA, mA, bitsB, mB, blocks)
+    b_slab = 4 * q * (R + D)  # bytes per apply, FP32
+
+    stream = torch.cuda.current_stream()
+    sv = trbl.Solver(th, w.nev, q, w.max_basis, w.tol, precision=trbl.TRBL_PREC_MIXED, seed=w.seed,
+                     check_every=1, stream=stream)
+    for _ in range(args.warmup):
+        sv.step()
+    torch.cuda.synchronize()
+    barrier()
+    st0 = sv.stats()
+    l0 = trbl.trbl_kernel_launches()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        sv.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = trbl.trbl_kernel_launches() - l0
+    st1 = sv.stats()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * nnz * q * args.steps / (ms * 1e-3) / 1e9
+    ms_apply = (st1["ms_apply"] - st0["ms_apply"]) / args.steps
+    achieved = b_slab / (ms_apply * 1e-3) / 1e9
+
+    # end to end: the same steps with V_k supplied from and V_{k+1} returned to
+    # pinned host memory through the C ABI (trbl_solver_step_host)
+    ptr, nbytes = sv.block()
+    host_in = torch.empty(nbytes // 4, dtype=torch.float32, pin_memory=True)
+    host_out = torch.empty_like(host_in, pin_memory=True)
+    sv.step_host(None, host_in)  # untimed: fills the host copy of the current block
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        src, dst = (host_in, host_out) if k % 2 == 0 else (host_out, host_in)
+        sv.step_host(src, dst)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([el], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    e2e_value = world * nnz * q * args.steps / el / 1e9
+
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "dim": D, "q": q, "nev": w.nev, "max_basis": w.max_basis,
+                   "precision": "mixed (FP32 vectors/apply, FP64 coefficients, CholQR2, Ritz)",
+                   "structural_nnz": nnz, "basis_fill_at_first_timed_step": q * (args.warmup + 1),
+                   "l2": "inputs larger than L2 (basis %.1f GB, block %.2f GB)"
+                         % (D * w.max_basis * 4 / 1e9, D * q * 4 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "apply": {"ms_per_launch": ms_apply, "gnzq_per_s": nnz * q / (ms_apply * 1e-3) / 1e9,
+                  "share_of_step": ms_apply / ms_step},
+        "phases_ms_per_step": {k: (st1[k] - st0[k]) / args.steps
+                               for k in ("ms_apply", "ms_orth", "ms_qr", "ms_ritz", "ms_restart")},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": ncu_traffic(),
+                     "kernel": "apply_rows_kernel<float>",
+                     "algorithmic_bytes_per_launch": b_slab,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"},
+        "clocks": clk,
+        "gpu_launches": int(launches),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes, "ms_per_step": el / args.steps * 1e3},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(WORKLOAD, q, args.cpu_seconds)
+    del sv
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_apply_only(args):
+    """Time the block product alone on one workload (used for kernel profiles)."""
+    import torch
+    import paper_1902_02064_gb300 as trbl
+    w, sa, sb, inter = synth.workload(args.apply_only)
+    q = args.q or w.q
+    tb = trbl.Basis(sa, w.nA, sb, w.nB, w.twoM)
+    th = trbl.Hamiltonian.from_interaction(tb, inter)
+    bitsA, mA, bitsB, mB, blocks = tb.export()
+    R = slab_rows(bitsA, mA, mB, w.twoM)
+    nnz = structural_nnz(bitsA, mA, bitsB, mB, blocks)
+    dt = torch.float64 if args.fp64 else torch.float32
+    g = torch.Generator(device="cuda")
+    g.manual_seed(w.seed)
+    V = torch.rand((tb.dim, q), generator=g, device="cuda", dtype=dt) * 2 - 1
+    W = torch.empty_like(V)
+    for _ in range(args.warmup):
+        th.apply(V, W)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        th.apply(V, W)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    b_slab = (8 if args.fp64 else 4) * q * (R + tb.dim)
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    print(json.dumps({"workload": args.apply_only, "dim": tb.dim, "q": q, "dtype": str(dt),
+                      "ms_per_apply": ms, "gnzq_per_s": nnz * q / (ms * 1e-3) / 1e9,
+                      "structural_nnz": nnz, "slab_rows_R": R, "algorithmic_bytes": b_slab,
+                      "achieved_gbs": b_slab / (ms * 1e-3) / 1e9, "frac_of_measured_hbm": b_slab / (ms * 1e-3) / 1e9 / peak}),
+          flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--apply-only", default=None, help="time only W = H V on this workload")
+    ap.add_argument("--q", type=int, default=0)
+    ap.add_argument("--fp64", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.apply_only:
+        run_apply_only(args)
+    elif args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -210,6 +210,11 @@ int trbl_solver_stats(trbl_solver* s, trbl_stats* stats);
 int trbl_solver_finish(trbl_solver* s, double* evals, double* resid, void* evecs, trbl_stats* stats);
 void trbl_solver_destroy(trbl_solver* s);
 
+/* Number of kernels this library has launched in the process so far
+ * (every entry point counts its own launches; library calls such as the
+ * cuSOLVER eigensolver are not counted). */
+long long trbl_kernel_launches(void);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* trbl_last_error(void);
 

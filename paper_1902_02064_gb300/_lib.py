@@ -81,6 +81,7 @@ def lib():
         "trbl_solver_stats": (C.c_int, [_VP, C.POINTER(trbl_stats)]),
         "trbl_solver_finish": (C.c_int, [_VP, _DP, _DP, _VP, C.POINTER(trbl_stats)]),
         "trbl_solver_destroy": (None, [_VP]),
+        "trbl_kernel_launches": (C.c_longlong, []),
         "trbl_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -89,6 +90,10 @@ def lib():
         f.argtypes = args
     _LIB = L
     return L
+
+
+def trbl_kernel_launches() -> int:
+    return int(lib().trbl_kernel_launches())
 
 
 def trbl_last_error() -> str:

@@ -110,7 +110,7 @@ int launch_typed(const DevH<T>& h, int64_t D, const T* V, int64_t ldv, T* W, int
   const int bs = 256;
   const int64_t grid = (threads + bs - 1) / bs;
   if (grid > 0x7fffffffLL) return fail(TRBL_ERR_ARG, "block too large for one launch");
-  apply_rows_kernel<T><<<unsigned(grid), bs, 0, s>>>(h, V, ldv, W, ldw, q, D);
+  apply_rows_kernel<T><<<unsigned(grid), bs, 0, s>>>(h, V, ldv, W, ldw, q, D); note_launch();
   TRBL_CUDA(cudaGetLastError());
   return TRBL_OK;
 }
@@ -212,11 +212,13 @@ int upload_tables(trbl_hamiltonian* h) {
   };
   fill(h->d64, o_hcA64, o_hcB64, o_vab64);
   fill(h->d32, o_hcA32, o_hcB32, o_vab32);
-  return TRBL_OK;
+  return upload_grouped(h);
 }
 
 int launch_apply(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, int64_t ldw,
                  int q, int dtype, cudaStream_t s) {
+  const int g = launch_grouped(h, V, ldv, W, ldw, q, dtype, s);
+  if (g != -1) return g;
   const int64_t D = h->b->D;
   if (dtype == TRBL_F64)
     return launch_typed<double>(h->d64, D, static_cast<const double*>(V), ldv,

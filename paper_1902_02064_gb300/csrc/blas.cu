@@ -192,10 +192,10 @@ int dot_launch(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, i
   const size_t need = size_t(nchunk) * m * q * sizeof(double);
   if (need > ws.partial_bytes) return fail(TRBL_ERR_ARG, "block_dot workspace too small");
   dim3 grid(mtiles, unsigned(nchunk));
-  block_dot_kernel<T, QP><<<grid, 32 * (QP / 4), 0, s>>>(B, ldb, m, W, ldw, q, D, rows, ws.partial);
+  block_dot_kernel<T, QP><<<grid, 32 * (QP / 4), 0, s>>>(B, ldb, m, W, ldw, q, D, rows, ws.partial); note_launch();
   TRBL_CUDA(cudaGetLastError());
   const int mq = m * q;
-  reduce_partials_kernel<<<(mq + 255) / 256, 256, 0, s>>>(ws.partial, int(nchunk), mq, C);
+  reduce_partials_kernel<<<(mq + 255) / 256, 256, 0, s>>>(ws.partial, int(nchunk), mq, C); note_launch();
   TRBL_CUDA(cudaGetLastError());
   return TRBL_OK;
 }
@@ -231,15 +231,15 @@ int rowgemm(const T* In, int64_t ldi, int K, const double* U, int64_t ldu, int n
   if (n <= 16) {
     constexpr int RT = 128, CT = 16;
     dim3 grid(unsigned((D + RT - 1) / RT), unsigned((n + CT - 1) / CT));
-    rowgemm_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta);
+    rowgemm_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta); note_launch();
   } else if (n <= 32) {
     constexpr int RT = 128, CT = 32;
     dim3 grid(unsigned((D + RT - 1) / RT), unsigned((n + CT - 1) / CT));
-    rowgemm_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta);
+    rowgemm_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta); note_launch();
   } else {
     constexpr int RT = 64, CT = 64;
     dim3 grid(unsigned((D + RT - 1) / RT), unsigned((n + CT - 1) / CT));
-    rowgemm_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta);
+    rowgemm_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta); note_launch();
   }
   TRBL_CUDA(cudaGetLastError());
   return TRBL_OK;
@@ -249,7 +249,7 @@ template <typename S, typename T>
 int copy_cols(const S* src, int64_t lds, T* dst, int64_t ldd, int64_t D, int ncol, cudaStream_t s) {
   if (ncol <= 0 || D <= 0) return TRBL_OK;
   const int64_t n = D * ncol;
-  copy_cols_kernel<S, T><<<unsigned((n + 255) / 256), 256, 0, s>>>(src, lds, dst, ldd, D, ncol);
+  copy_cols_kernel<S, T><<<unsigned((n + 255) / 256), 256, 0, s>>>(src, lds, dst, ldd, D, ncol); note_launch();
   TRBL_CUDA(cudaGetLastError());
   return TRBL_OK;
 }
@@ -258,7 +258,7 @@ template <typename T>
 int random_block(T* X, int64_t ldx, int64_t D, int ncol, int ncol_total, int col0, uint64_t seed,
                  cudaStream_t s) {
   const int64_t n = D * ncol;
-  random_block_kernel<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(X, ldx, D, ncol, ncol_total, col0, seed);
+  random_block_kernel<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(X, ldx, D, ncol, ncol_total, col0, seed); note_launch();
   TRBL_CUDA(cudaGetLastError());
   return TRBL_OK;
 }

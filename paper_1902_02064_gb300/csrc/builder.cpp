@@ -12,6 +12,7 @@
 //   locates the target by binary search (App. B.1), which is what `find`
 //   does here, once, at build time.
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -23,6 +24,9 @@
 namespace trbl {
 
 static thread_local std::string g_err;
+static std::atomic<long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int fail(int code, const char* fmt, ...) {
   char buf[512];
@@ -194,6 +198,8 @@ using namespace trbl;
 
 extern "C" const char* trbl_last_error(void) { return g_err.c_str(); }
 
+extern "C" long long trbl_kernel_launches(void) { return g_launches.load(); }
+
 extern "C" int trbl_basis_create(const trbl_space* A, const trbl_space* B, int twoM,
                                  trbl_basis** out) {
   clear_error();
@@ -244,6 +250,8 @@ extern "C" int trbl_basis_create(const trbl_space* A, const trbl_space* B, int t
       for (int j = 0; j < nblk; ++j)
         if (b->blocks[j].mA == mA) b->srcblk[size_t(k) * b->ND + di] = j;
     }
+  for (int s = 0; s < 2; ++s)
+    for (int c : b->sp[s].gcount) b->max_group = std::max(b->max_group, c);
   build_jumps(&b->sp[0], span, b->ND);
   build_jumps(&b->sp[1], span, b->ND);
   *out = b;
@@ -399,9 +407,8 @@ extern "C" int trbl_hamiltonian_create(const trbl_basis* b, const double* h1A, c
 
 extern "C" void trbl_hamiltonian_destroy(trbl_hamiltonian* h) {
   if (!h) return;
-  if (h->arena) {
-    cudaDeviceSynchronize();
-    cudaFree(h->arena);
-  }
+  if (h->arena || h->garena) cudaDeviceSynchronize();
+  if (h->arena) cudaFree(h->arena);
+  if (h->garena) cudaFree(h->garena);
   delete h;
 }

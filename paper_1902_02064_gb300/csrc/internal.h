@@ -15,6 +15,8 @@ namespace trbl {
 int fail(int code, const char* fmt, ...);
 // Clears the thread's error message (start of every entry point).
 void clear_error();
+// Counts one launch of a library kernel (trbl_kernel_launches).
+void note_launch();
 // TRBL_ERR_CUDA with the call site and CUDA's message when e != cudaSuccess.
 int cuda_fail(cudaError_t e, const char* what);
 
@@ -59,6 +61,7 @@ struct trbl_basis {
   std::vector<trbl::Block> blocks;
   std::vector<int32_t> srcblk;  // [blk*ND + di]: block holding M_A - delta, or -1
   int64_t D = 0;
+  int max_group = 0;  // largest 2M group of either species
 };
 
 namespace trbl {
@@ -88,6 +91,16 @@ struct DevH {
   const T* vab;
 };
 
+// Extra tables of the grouped block-product kernel (apply_grouped.cu).
+template <typename T>
+struct DevG {
+  const int4* work;     // (target A determinant, block, first neutron row, row count)
+  int nwork;
+  int maxP, maxQ, maxK; // per-target proton jumps, like-particle A sources, coefficient row length
+  const int2* jB2;      // neutron jumps: (source local index, (k << 1) | negative), k = pair index in its 2m-transfer class
+  const T* ccoef;       // ccoef[(a*nA + c) * maxK + k] = V^AB_{a b_k, c d_k} for the class of transfer m_c - m_a
+};
+
 }  // namespace trbl
 
 struct trbl_hamiltonian {
@@ -101,12 +114,21 @@ struct trbl_hamiltonian {
   void* arena = nullptr;
   trbl::DevH<double> d64;
   trbl::DevH<float> d32;
+  trbl::DevG<double> g64;
+  trbl::DevG<float> g32;
+  void* garena = nullptr;
   size_t arena_bytes = 0;
 };
 
 namespace trbl {
 // Uploads the tables of h to the current device (apply.cu).
 int upload_tables(trbl_hamiltonian* h);
+// Builds and uploads the grouped-kernel tables (apply_grouped.cu).
+int upload_grouped(trbl_hamiltonian* h);
+// Enqueues W = H V with the grouped kernel when q and the alignment allow it;
+// returns -1 (nothing launched) otherwise.
+int launch_grouped(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, int64_t ldw, int q,
+                   int dtype, cudaStream_t s);
 // Enqueues W = H V (apply.cu).
 int launch_apply(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, int64_t ldw,
                  int q, int dtype, cudaStream_t s);

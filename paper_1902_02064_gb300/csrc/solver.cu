@@ -308,16 +308,16 @@ struct Solver {
   // deficient columns found in pass 1 (their flags stay in hflags).
   int cholqr2(T* Win, double thresh_abs, double thresh_rel, int* ndef) {
     TRY(block_dot<T>(Win, q, q, Win, q, q, D, G, ws, s));
-    chol_kernel<<<1, 64, 0, s>>>(G, q, thresh_abs, thresh_rel, R1, R1i, flags + kF1);
+    chol_kernel<<<1, 64, 0, s>>>(G, q, thresh_abs, thresh_rel, R1, R1i, flags + kF1); note_launch();
     TRBL_CUDA(cudaGetLastError());
     TRBL_CUDA(cudaMemcpyAsync(hflags + kF1, flags + kF1, sizeof(int) * (q + 1), cudaMemcpyDeviceToHost, s));
     TRY(rowgemm<T>(Win, q, q, R1i, q, q, W2, q, D, 1.0, 0.0, s));
     TRY(block_dot<T>(W2, q, q, W2, q, q, D, G, ws, s));
-    chol_kernel<<<1, 64, 0, s>>>(G, q, 0.0, 1e-3, R2, R2i, flags + kF2);
+    chol_kernel<<<1, 64, 0, s>>>(G, q, 0.0, 1e-3, R2, R2i, flags + kF2); note_launch();
     TRBL_CUDA(cudaGetLastError());
     TRBL_CUDA(cudaMemcpyAsync(hflags + kF2, flags + kF2, sizeof(int), cudaMemcpyDeviceToHost, s));
     TRY(rowgemm<T>(W2, q, q, R2i, q, q, Vk, q, D, 1.0, 0.0, s));
-    upper_mul_kernel<<<(q * q + 127) / 128, 128, 0, s>>>(R2, R1, q, beta);
+    upper_mul_kernel<<<(q * q + 127) / 128, 128, 0, s>>>(R2, R1, q, beta); note_launch();
     TRBL_CUDA(cudaGetLastError());
     TRBL_CUDA(cudaStreamSynchronize(s));
     *ndef = hflags[kF1] + hflags[kF2];
@@ -351,7 +351,7 @@ struct Solver {
     TRBL_SOLVER(cusolverDnDsyevd(sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nb, Aw, mb, theta,
                                  syev_work, lwork, devinfo));
     const int n = std::min(nev, nb);
-    ritz_resid_kernel<<<(n + 127) / 128, 128, 0, s>>>(beta, q, Aw, mb, nb, n, res);
+    ritz_resid_kernel<<<(n + 127) / 128, 128, 0, s>>>(beta, q, Aw, mb, nb, n, res); note_launch();
     TRBL_CUDA(cudaGetLastError());
     TRBL_CUDA(cudaMemcpyAsync(hbuf, theta, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
     TRBL_CUDA(cudaMemcpyAsync(hbuf + mb, res, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
@@ -365,7 +365,7 @@ struct Solver {
 
   // basis[:, 0:n_out] <- basis[:, 0:nb] U[:, 0:n_out] in row panels
   int compress(int nb, int n_out) {
-    transpose_kernel<<<(nb * n_out + 255) / 256, 256, 0, s>>>(Aw, mb, nb, n_out, Ut);
+    transpose_kernel<<<(nb * n_out + 255) / 256, 256, 0, s>>>(Aw, mb, nb, n_out, Ut); note_launch();
     TRBL_CUDA(cudaGetLastError());
     for (int64_t r0 = 0; r0 < D; r0 += panel_rows) {
       const int64_t nr = std::min(panel_rows, D - r0);
@@ -413,7 +413,7 @@ struct Solver {
     tm.rec(1, s);
     double* C1 = C + size_t(2) * mb * q;
     TRY(cgs2(W, nb, C1));
-    set_alpha_kernel<<<(q * q + 127) / 128, 128, 0, s>>>(Tm, mb, C1, nb - q, q);
+    set_alpha_kernel<<<(q * q + 127) / 128, 128, 0, s>>>(Tm, mb, C1, nb - q, q); note_launch();
     TRBL_CUDA(cudaGetLastError());
     tm.rec(2, s);
     TRY(block_qr(nb));
@@ -439,14 +439,14 @@ struct Solver {
         trace("restart nb %d -> %d", nb, ls + q);
         TRY(compress(nb, ls));
         TRBL_CUDA(cudaMemsetAsync(Tm, 0, sizeof(double) * mb * mb, s));
-        restart_t_kernel<<<(ls * q + 127) / 128, 128, 0, s>>>(Tm, mb, theta, beta, q, Aw, mb, nb, ls);
+        restart_t_kernel<<<(ls * q + 127) / 128, 128, 0, s>>>(Tm, mb, theta, beta, q, Aw, mb, nb, ls); note_launch();
         TRBL_CUDA(cudaGetLastError());
         TRY(copy_cols<T, T>(Vk, q, basis + ls, mb, D, q, s));
         nb = ls + q;
         have_ritz = false;
         ++restarts;
       } else {
-        set_beta_kernel<<<(q * q + 127) / 128, 128, 0, s>>>(Tm, mb, beta, nb, nb - q, q);
+        set_beta_kernel<<<(q * q + 127) / 128, 128, 0, s>>>(Tm, mb, beta, nb, nb - q, q); note_launch();
         TRBL_CUDA(cudaGetLastError());
         TRY(copy_cols<T, T>(Vk, q, basis + nb, mb, D, q, s));
         nb += q;
@@ -488,7 +488,7 @@ struct Solver {
     const int n = std::min(nev, nr);
     for (int i = 0; i < n; ++i) evals[i] = hbuf[i];
     for (int i = n; i < nev; ++i) evals[i] = NAN;
-    transpose_kernel<<<(nr * n + 255) / 256, 256, 0, s>>>(Aw, mb, nr, n, Ut);
+    transpose_kernel<<<(nr * n + 255) / 256, 256, 0, s>>>(Aw, mb, nr, n, Ut); note_launch();
     TRBL_CUDA(cudaGetLastError());
     if (evecs) TRY(rowgemm<T>(basis, mb, nr, Ut, n, n, static_cast<T*>(evecs), nev, D, 1.0, 0.0, s));
     if (resid) {
@@ -504,9 +504,9 @@ struct Solver {
           TRY(copy_cols<T, double>(W, nc, Xd, nc, D, nc, s));
         }
         TRY(launch_apply(h, Xd, nc, HXd, nc, nc, TRBL_F64, s));
-        resid_partial_kernel<<<unsigned(nchunk), 64, 0, s>>>(HXd, Xd, nc, theta + c0, D, rows, rpart);
+        resid_partial_kernel<<<unsigned(nchunk), 64, 0, s>>>(HXd, Xd, nc, theta + c0, D, rows, rpart); note_launch();
         TRBL_CUDA(cudaGetLastError());
-        resid_final_kernel<<<1, 64, 0, s>>>(rpart, int(nchunk), nc, rtrue + c0);
+        resid_final_kernel<<<1, 64, 0, s>>>(rpart, int(nchunk), nc, rtrue + c0); note_launch();
         TRBL_CUDA(cudaGetLastError());
       }
       TRBL_CUDA(cudaMemcpyAsync(resid, rtrue, sizeof(double) * n, cudaMemcpyDeviceToHost, s));

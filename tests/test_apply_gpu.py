@@ -163,3 +163,38 @@ def test_apply_full_size_sampled_rows(name, q, dtype):
     Hx, Hy = th.apply(x), th.apply(y)
     a, b = torch.dot(x[:, 0], Hy[:, 0]).item(), torch.dot(Hx[:, 0], y[:, 0]).item()
     assert abs(a - b) <= 1e-10 * (abs(a) + abs(b))
+
+
+@pytest.mark.parametrize("kA,kB,twoM,q,dtype", [(0, 2, 0, 4, torch.float32), (2, 0, 0, 2, torch.float64),
+                                                (1, 1, 2, 8, torch.float32), (3, 2, 1, 16, torch.float64)])
+def test_apply_edge_cases_grouped_path(kA, kB, twoM, q, dtype):
+    """Row sizes that are multiples of 16 bytes take the grouped kernel."""
+    sp = synth.make_space(synth.SPACE12_SHELLS)
+    inter = synth.draw_interaction(sp, sp, 33)
+    B = ob.ProductBasis(sp.twom, kA, sp.twom, kB, twoM)
+    H = oh.assemble(B, inter)
+    tb = trbl.Basis(sp, kA, sp, kB, twoM)
+    th = trbl.Hamiltonian.from_interaction(tb, inter)
+    V = torch.from_numpy(synth.random_block(B.dim, q, 2)).to(dtype)
+    W = th.apply(V.cuda())
+    torch.cuda.synchronize()
+    _check(W.cpu().numpy(), H, V.numpy(), dtype)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_grouped_and_row_kernels_agree(medium, dtype):
+    """Aligned rows (grouped kernel) against a leading dimension that is not a
+    multiple of 16 bytes (row kernel): same products to rounding."""
+    w, B, H, tb, th = medium
+    q = 16
+    Vb = torch.from_numpy(synth.random_block(B.dim, q + 1, 8)).to(dtype).cuda()
+    Va = Vb[:, :q].contiguous()
+    Wa = th.apply(Va)
+    Wr = torch.empty((B.dim, q + 1), dtype=dtype, device="cuda")
+    trbl.trbl_apply_block(th.handle, Vb.data_ptr(), q + 1, Wr.data_ptr(), q + 1, q,
+                          trbl.TRBL_F64 if dtype == torch.float64 else trbl.TRBL_F32,
+                          torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    bound = torch.from_numpy(abs(H) @ np.abs(Va.double().cpu().numpy())).cuda()
+    diff = (Wa.double() - Wr[:, :q].double()).abs()
+    assert torch.all(diff <= 2 * RTOL[dtype] * bound)
