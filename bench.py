@@ -284,8 +284,8 @@ def run_ours(args, rank, world):
         if dist is not None:
             dist.barrier()
 
-    w, sa, sb, inter = synth.workload(WORKLOAD)
-    q = w.q
+    w, sa, sb, inter = synth.workload(args.workload)
+    q = args.q or w.q
     tb = trbl.Basis(sa, w.nA, sb, w.nB, w.twoM)
     th = trbl.Hamiltonian.from_interaction(tb, inter)
     D = tb.dim
@@ -354,7 +354,7 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "dim": D, "q": q, "nev": w.nev, "max_basis": w.max_basis,
+        "config": {"workload": args.workload, "dim": D, "q": q, "nev": w.nev, "max_basis": w.max_basis,
                    "precision": "mixed (FP32 vectors/apply, FP64 coefficients, CholQR2, Ritz)",
                    "structural_nnz": nnz, "basis_fill_at_first_timed_step": q * (args.warmup + 1),
                    "l2": "inputs larger than L2 (basis %.1f GB, block %.2f GB)"
@@ -375,7 +375,7 @@ def run_ours(args, rank, world):
                 "d2h_bytes_per_step": nbytes, "ms_per_step": el / args.steps * 1e3},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(WORKLOAD, q, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(args.workload, q, args.cpu_seconds)
     del sv
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -429,6 +429,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--apply-only", default=None, help="time only W = H V on this workload")
+    ap.add_argument("--workload", default=WORKLOAD, help="workload of the solver steps (default: the 5+5 space)")
     ap.add_argument("--q", type=int, default=0)
     ap.add_argument("--fp64", action="store_true")
     args = ap.parse_args()

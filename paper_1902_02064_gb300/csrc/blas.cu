@@ -9,6 +9,8 @@
 // In FP32 storage the products are FP32 FMAs summed in two FP32 levels per
 // thread block, and the per-block partial sums are reduced across blocks in
 // FP64 in a fixed order (deterministic).
+#include <algorithm>
+
 #include "blas.cuh"
 
 namespace trbl {
@@ -16,6 +18,24 @@ namespace trbl {
 namespace {
 
 constexpr int MT = 128;  // stored vectors per block_dot tile
+
+// Four consecutive values from shared memory as 16-byte vector loads
+// (address 16-byte aligned).
+__device__ __forceinline__ void lds4(const float* p, float (&x)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  x[0] = v.x;
+  x[1] = v.y;
+  x[2] = v.z;
+  x[3] = v.w;
+}
+__device__ __forceinline__ void lds4(const double* p, double (&x)[4]) {
+  const double2 v0 = *reinterpret_cast<const double2*>(p);
+  const double2 v1 = *reinterpret_cast<const double2*>(p + 2);
+  x[0] = v0.x;
+  x[1] = v0.y;
+  x[2] = v1.x;
+  x[3] = v1.y;
+}
 
 template <typename T>
 struct DotCfg;
@@ -65,8 +85,8 @@ __global__ void __launch_bounds__(32 * (QP / 4)) block_dot_kernel(
 #pragma unroll 4
     for (int rr = 0; rr < RS; ++rr) {
       T b[4], w[4];
-      for (int i = 0; i < 4; ++i) b[i] = Bs[rr][4 * tm + i];
-      for (int j = 0; j < 4; ++j) w[j] = Ws[rr][4 * tq + j];
+      lds4(&Bs[rr][4 * tm], b);
+      lds4(&Ws[rr][4 * tq], w);
       for (int i = 0; i < 4; ++i)
         for (int j = 0; j < 4; ++j) t[i][j] = fma(b[i], w[j], t[i][j]);
     }
@@ -126,8 +146,8 @@ __global__ void __launch_bounds__(RT * CT / 16) rowgemm_kernel(
 #pragma unroll 4
     for (int kk = 0; kk < KC; ++kk) {
       T b[4], u[4];
-      for (int i = 0; i < 4; ++i) b[i] = Bs[kk][4 * tr + i];
-      for (int j = 0; j < 4; ++j) u[j] = Us[kk][4 * tc + j];
+      lds4(&Bs[kk][4 * tr], b);
+      lds4(&Us[kk][4 * tc], u);
       for (int i = 0; i < 4; ++i)
         for (int j = 0; j < 4; ++j) acc[i][j] = fma(b[i], u[j], acc[i][j]);
     }
@@ -144,6 +164,98 @@ __global__ void __launch_bounds__(RT * CT / 16) rowgemm_kernel(
       *o = (beta == 0.0) ? v : fma(T(beta), *o, v);
     }
   }
+}
+
+// Tall-skinny Out[:, 0:n] = alpha * In[:, 0:K] U + beta * Out with n <= NP <= 64:
+// U (K x n, FP64) is converted once per thread block into shared memory;
+// persistent blocks stride over row tiles of RT rows; the In tile of the
+// next K-chunk is fetched into registers while the current one is used.
+template <typename T, int NP>
+__global__ void __launch_bounds__(512) rowgemm_tall_kernel(const T* __restrict__ In, int64_t ldi, int K,
+                                                           const double* __restrict__ U, int64_t ldu, int n,
+                                                           T* __restrict__ Out, int64_t ldo, int64_t D,
+                                                           double alpha, double beta) {
+  constexpr int NT = 512, KC = 32;
+  constexpr int TC = NP / 4, TR = NT / TC, RT = 4 * TR;
+  constexpr int LD = RT + 4;
+  constexpr int PER = RT * KC / NT;  // In elements each thread fetches per chunk
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Us = reinterpret_cast<T*>(smem_raw);  // [Kp * NP], Kp = K rounded up to KC
+  const int Kp = (K + KC - 1) / KC * KC;
+  T* Bs = Us + size_t(Kp) * NP;            // [2][KC][LD]
+  const int tid = threadIdx.x;
+  for (int i = tid; i < Kp * NP; i += NT) {
+    const int k = i / NP, c = i - k * NP;
+    Us[i] = (k < K && c < n) ? T(U[int64_t(k) * ldu + c]) : T(0);
+  }
+  const int tr = tid % TR, tc = tid / TR;
+  const int64_t ntiles = (D + RT - 1) / RT;
+  const T al = T(alpha), be = T(beta);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t r0 = tile * RT;
+    T acc[4][4];
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    T pre[PER];
+    auto fetch = [&](int k0) {
+#pragma unroll
+      for (int e = 0; e < PER; ++e) {
+        const int idx = tid + e * NT;
+        const int rr = idx / KC, kk = idx - rr * KC;
+        const int64_t r = r0 + rr;
+        pre[e] = (r < D && k0 + kk < K) ? In[r * ldi + k0 + kk] : T(0);
+      }
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+      for (int e = 0; e < PER; ++e) {
+        const int idx = tid + e * NT;
+        const int rr = idx / KC, kk = idx - rr * KC;
+        Bs[(buf * KC + kk) * LD + rr] = pre[e];
+      }
+    };
+    fetch(0);
+    __syncthreads();  // Us ready; previous tile's readers of Bs are done
+    stash(0);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = 0; k0 < K; k0 += KC) {
+      const bool more = k0 + KC < K;
+      if (more) fetch(k0 + KC);
+      const T* B0 = Bs + buf * KC * LD + 4 * tr;
+      const T* U0 = Us + size_t(k0) * NP + 4 * tc;
+#pragma unroll 8
+      for (int kk = 0; kk < KC; ++kk) {
+        T b[4], u[4];
+        lds4(B0 + kk * LD, b);
+        lds4(U0 + kk * NP, u);
+        for (int i = 0; i < 4; ++i)
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(b[i], u[j], acc[i][j]);
+      }
+      if (more) {
+        stash(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+      }
+    }
+    for (int i = 0; i < 4; ++i) {
+      const int64_t r = r0 + 4 * tr + i;
+      if (r >= D) continue;
+      for (int j = 0; j < 4; ++j) {
+        const int c = 4 * tc + j;
+        if (c >= n) continue;
+        T* o = Out + r * ldo + c;
+        const T v = al * acc[i][j];
+        *o = (beta == 0.0) ? v : fma(be, *o, v);
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void scale_col_kernel(T* __restrict__ X, int64_t ldx, int64_t D, double a) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r < D) X[r * ldx] = T(a * double(X[r * ldx]));
 }
 
 template <typename S, typename T>
@@ -220,6 +332,23 @@ int block_dot(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, in
   return fail(TRBL_ERR_ARG, "block_dot: q=%d > 64", q);
 }
 
+template <typename T, int NP>
+int tall_launch(const T* In, int64_t ldi, int K, const double* U, int64_t ldu, int n, T* Out, int64_t ldo,
+                int64_t D, double alpha, double beta, cudaStream_t s, size_t smem, int sms) {
+  static bool configured = false;
+  if (!configured) {
+    TRBL_CUDA(cudaFuncSetAttribute(rowgemm_tall_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   228 * 1024 - 1024));
+    configured = true;
+  }
+  constexpr int RT = 4 * (512 / (NP / 4));
+  const int64_t ntiles = (D + RT - 1) / RT;
+  const int grid = int(std::min<int64_t>(ntiles, sms));
+  rowgemm_tall_kernel<T, NP><<<grid, 512, smem, s>>>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta); note_launch();
+  TRBL_CUDA(cudaGetLastError());
+  return TRBL_OK;
+}
+
 template <typename T>
 int rowgemm(const T* In, int64_t ldi, int K, const double* U, int64_t ldu, int n, T* Out,
             int64_t ldo, int64_t D, double alpha, double beta, cudaStream_t s) {
@@ -227,6 +356,24 @@ int rowgemm(const T* In, int64_t ldi, int K, const double* U, int64_t ldu, int n
   if (K <= 0) {
     // Out = beta * Out
     if (beta == 1.0) return TRBL_OK;
+  }
+  if (K > 0 && n <= 64) {
+    const int NP = n <= 16 ? 16 : (n <= 32 ? 32 : 64);
+    const int RT = 4 * (512 / (NP / 4));
+    const int Kp = (K + 31) / 32 * 32;
+    const size_t smem = (size_t(Kp) * NP + size_t(2) * 32 * (RT + 4)) * sizeof(T);
+    if (smem <= 200 * 1024) {
+      static int sms = 0;
+      if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+      }
+      if (NP == 16) return tall_launch<T, 16>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta, s, smem, sms);
+      if (NP == 32) return tall_launch<T, 32>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta, s, smem, sms);
+      return tall_launch<T, 64>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta, s, smem, sms);
+    }
   }
   if (n <= 16) {
     constexpr int RT = 128, CT = 16;
@@ -255,6 +402,13 @@ int copy_cols(const S* src, int64_t lds, T* dst, int64_t ldd, int64_t D, int nco
 }
 
 template <typename T>
+int scale_col(T* X, int64_t ldx, int64_t D, double a, cudaStream_t s) {
+  scale_col_kernel<T><<<unsigned((D + 255) / 256), 256, 0, s>>>(X, ldx, D, a); note_launch();
+  TRBL_CUDA(cudaGetLastError());
+  return TRBL_OK;
+}
+
+template <typename T>
 int random_block(T* X, int64_t ldx, int64_t D, int ncol, int ncol_total, int col0, uint64_t seed,
                  cudaStream_t s) {
   const int64_t n = D * ncol;
@@ -272,6 +426,8 @@ template int copy_cols<double, double>(const double*, int64_t, double*, int64_t,
 template int copy_cols<float, double>(const float*, int64_t, double*, int64_t, int64_t, int, cudaStream_t);
 template int copy_cols<double, float>(const double*, int64_t, float*, int64_t, int64_t, int, cudaStream_t);
 template int random_block<float>(float*, int64_t, int64_t, int, int, int, uint64_t, cudaStream_t);
+template int scale_col<float>(float*, int64_t, int64_t, double, cudaStream_t);
+template int scale_col<double>(double*, int64_t, int64_t, double, cudaStream_t);
 template int random_block<double>(double*, int64_t, int64_t, int, int, int, uint64_t, cudaStream_t);
 
 }  // namespace trbl

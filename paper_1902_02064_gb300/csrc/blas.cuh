@@ -30,6 +30,10 @@ int rowgemm(const T* In, int64_t ldi, int K, const double* U, int64_t ldu, int n
 template <typename S, typename T>
 int copy_cols(const S* src, int64_t lds, T* dst, int64_t ldd, int64_t D, int ncol, cudaStream_t s);
 
+// X[:, 0] *= a (one column, leading dimension ldx).
+template <typename T>
+int scale_col(T* X, int64_t ldx, int64_t D, double a, cudaStream_t s);
+
 // Seeded uniform(-1, 1) block: entry (r, col0 + c) uses counter
 // (seed << 32) + r * ncol_total + col0 + c through splitmix64.
 template <typename T>

@@ -23,6 +23,7 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -51,12 +52,16 @@ namespace {
   } while (0)
 
 // Cholesky G = R^T R (R upper) of a q x q FP64 Gram matrix, R^{-1}, and
-// per-column deficiency flags: pivot^2 <= thresh2[j] marks column j.
+// per-column deficiency flags: column j is marked when its pivot is at most
+// thresh_abs, or thresh_rel times its own norm, or thresh_max times the
+// largest column norm of the block.
 // One block of 64 threads; flags[0] counts deficient columns, flags[1+j] marks them.
 __global__ void chol_kernel(const double* __restrict__ G, int q, double thresh_abs, double thresh_rel,
-                            double* __restrict__ R, double* __restrict__ Rinv, int* __restrict__ flags) {
+                            double thresh_max, double* __restrict__ R, double* __restrict__ Rinv,
+                            int* __restrict__ flags) {
   __shared__ double Rs[64][65];
   __shared__ double diag0[64];
+  __shared__ double dmax;
   const int t = threadIdx.x;
   for (int i = t; i < q * q; i += blockDim.x) {
     const int r = i / q, c = i - r * q;
@@ -66,11 +71,18 @@ __global__ void chol_kernel(const double* __restrict__ G, int q, double thresh_a
   if (t == 0) flags[0] = 0;
   if (t < q) flags[1 + t] = 0;
   __syncthreads();
+  if (t == 0) {
+    double m = 0.0;
+    for (int j = 0; j < q; ++j) m = fmax(m, diag0[j]);
+    dmax = m;
+  }
+  __syncthreads();
   for (int j = 0; j < q; ++j) {
     if (t == 0) {
       double d = Rs[j][j];
       for (int k = 0; k < j; ++k) d -= Rs[k][j] * Rs[k][j];
-      const double lim = fmax(thresh_abs * thresh_abs, thresh_rel * thresh_rel * fmax(diag0[j], 0.0));
+      const double lim = fmax(fmax(thresh_abs * thresh_abs, thresh_rel * thresh_rel * fmax(diag0[j], 0.0)),
+                              thresh_max * thresh_max * dmax);
       if (!(d > lim)) {
         flags[0] += 1;
         flags[1 + j] = 1;
@@ -267,7 +279,8 @@ struct Solver {
   cudaStream_t s;
   int64_t D;
   int q, nev, mb, ls, dtype;
-  double tau;  // pass-1 deficiency threshold relative to ||H||
+  double tau;      // pass-1 deficiency threshold relative to ||H||
+  double tau_max;  // pass-1 deficiency threshold relative to the block's largest column
   Workspace ws;
   Arena ar;
   T *basis, *Vk, *W, *W2, *Wsave, *panel;
@@ -306,14 +319,14 @@ struct Solver {
 
   // Cholesky QR twice: Vk = W R^{-1}, beta = R2 R1.  Returns the number of
   // deficient columns found in pass 1 (their flags stay in hflags).
-  int cholqr2(T* Win, double thresh_abs, double thresh_rel, int* ndef) {
+  int cholqr2(T* Win, double thresh_abs, double thresh_rel, double thresh_max, int* ndef) {
     TRY(block_dot<T>(Win, q, q, Win, q, q, D, G, ws, s));
-    chol_kernel<<<1, 64, 0, s>>>(G, q, thresh_abs, thresh_rel, R1, R1i, flags + kF1); note_launch();
+    chol_kernel<<<1, 64, 0, s>>>(G, q, thresh_abs, thresh_rel, thresh_max, R1, R1i, flags + kF1); note_launch();
     TRBL_CUDA(cudaGetLastError());
     TRBL_CUDA(cudaMemcpyAsync(hflags + kF1, flags + kF1, sizeof(int) * (q + 1), cudaMemcpyDeviceToHost, s));
     TRY(rowgemm<T>(Win, q, q, R1i, q, q, W2, q, D, 1.0, 0.0, s));
     TRY(block_dot<T>(W2, q, q, W2, q, q, D, G, ws, s));
-    chol_kernel<<<1, 64, 0, s>>>(G, q, 0.0, 1e-3, R2, R2i, flags + kF2); note_launch();
+    chol_kernel<<<1, 64, 0, s>>>(G, q, 0.0, 1e-3, 0.0, R2, R2i, flags + kF2); note_launch();
     TRBL_CUDA(cudaGetLastError());
     TRBL_CUDA(cudaMemcpyAsync(hflags + kF2, flags + kF2, sizeof(int), cudaMemcpyDeviceToHost, s));
     TRY(rowgemm<T>(W2, q, q, R2i, q, q, Vk, q, D, 1.0, 0.0, s));
@@ -324,21 +337,55 @@ struct Solver {
     return TRBL_OK;
   }
 
-  // QR of W (already orthogonal to the basis) with repair of deficient columns.
+  // QR of W (already orthogonal to the basis).  Cholesky QR twice when the
+  // block is well conditioned; otherwise the column-wise path below.
   int block_qr(int nb) {
     int ndef = 0;
-    TRY(cholqr2(W, tau * normH, 0.0, &ndef));
+    TRY(cholqr2(W, tau * normH, 0.0, tau_max, &ndef));
     if (ndef == 0) return TRBL_OK;
-    // Keep W; replace the deficient columns by seeded random vectors,
-    // orthogonalise against the basis, QR again, and set beta = V_{k+1}^T W.
+    return column_qr(nb);
+  }
+
+  // Stable column-by-column QR of W: classical Gram-Schmidt twice against
+  // the basis and the earlier columns.  A column whose residual is at most
+  // tau * ||H|| (an exhausted Krylov direction) is replaced by a seeded
+  // random vector orthogonalised the same way.  beta_k = V_{k+1}^T W holds
+  // exactly because every dropped residual is negligible.
+  int column_qr(int nb) {
+    trace("column QR at nb %d", nb);
     TRBL_CUDA(cudaMemcpyAsync(Wsave, W, sizeof(T) * D * q, cudaMemcpyDeviceToDevice, s));
-    std::vector<int> bad;
-    for (int j = 0; j < q; ++j)
-      if (hflags[kF1 + 1 + j] || hflags[kF2]) bad.push_back(j);
-    for (int j : bad) TRY(random_block<T>(W + j, q, D, 1, q, j, p->seed + 0x9e37ull * (++reseed), s));
-    TRY(cgs2(W, nb, nullptr));
-    TRY(cholqr2(W, 0.0, 1e-6, &ndef));
-    if (ndef) return fail(TRBL_ERR_BREAKDOWN, "block QR: block stays rank deficient after repair");
+    TRY(block_dot<T>(W, q, q, W, q, q, D, G, ws, s));
+    TRBL_CUDA(cudaMemcpyAsync(hbuf, G, sizeof(double) * q * q, cudaMemcpyDeviceToHost, s));
+    TRBL_CUDA(cudaStreamSynchronize(s));
+    double cmax = 0.0;
+    for (int j = 0; j < q; ++j) cmax = std::max(cmax, std::sqrt(std::max(hbuf[j * q + j], 0.0)));
+    const double thr = std::max(tau * normH, (dtype == TRBL_F64 ? 1e-13 : 1e-6) * cmax);
+    for (int j = 0; j < q; ++j) {
+      T* wj = W + j;
+      for (int attempt = 0; attempt < 2; ++attempt) {
+        for (int pass = 0; pass < 2; ++pass) {
+          if (nb > 0) {
+            TRY(block_dot<T>(basis, mb, nb, wj, q, 1, D, C, ws, s));
+            TRY(rowgemm<T>(basis, mb, nb, C, 1, 1, wj, q, D, -1.0, 1.0, s));
+          }
+          if (j > 0) {
+            TRY(block_dot<T>(W, q, j, wj, q, 1, D, C, ws, s));
+            TRY(rowgemm<T>(W, q, j, C, 1, 1, wj, q, D, -1.0, 1.0, s));
+          }
+        }
+        TRY(block_dot<T>(wj, q, 1, wj, q, 1, D, G, ws, s));
+        TRBL_CUDA(cudaMemcpyAsync(hbuf, G, sizeof(double), cudaMemcpyDeviceToHost, s));
+        TRBL_CUDA(cudaStreamSynchronize(s));
+        const double nrm = std::sqrt(std::max(hbuf[0], 0.0));
+        if (nrm > thr || (attempt == 1 && nrm > 0.0)) {
+          TRY(scale_col<T>(wj, q, D, 1.0 / nrm, s));
+          break;
+        }
+        if (attempt == 1) return fail(TRBL_ERR_BREAKDOWN, "block QR: no new direction left (basis spans the space?)");
+        TRY(random_block<T>(wj, q, D, 1, q, j, p->seed + 0x9e37ull * (++reseed), s));
+      }
+    }
+    TRBL_CUDA(cudaMemcpyAsync(Vk, W, sizeof(T) * D * q, cudaMemcpyDeviceToDevice, s));
     TRY(block_dot<T>(Vk, q, q, Wsave, q, q, D, beta, ws, s));
     return TRBL_OK;
   }
@@ -346,10 +393,16 @@ struct Solver {
   // Eigenpairs of T[0:nb, 0:nb]; copies theta[0:nev], theta[nb-1] and the
   // residual estimates res[0:nev] to the host.
   int ritz(int nb) {
+    const auto w0 = std::chrono::steady_clock::now();
     TRBL_CUDA(cudaMemcpy2DAsync(Aw, sizeof(double) * mb, Tm, sizeof(double) * mb, sizeof(double) * nb, nb,
                                 cudaMemcpyDeviceToDevice, s));
     TRBL_SOLVER(cusolverDnDsyevd(sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nb, Aw, mb, theta,
                                  syev_work, lwork, devinfo));
+    if (trace_on()) {
+      cudaStreamSynchronize(s);
+      trace("ritz nb %d: syevd wall %.2f ms", nb,
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count());
+    }
     const int n = std::min(nev, nb);
     ritz_resid_kernel<<<(n + 127) / 128, 128, 0, s>>>(beta, q, Aw, mb, nb, n, res); note_launch();
     TRBL_CUDA(cudaGetLastError());
@@ -391,8 +444,8 @@ struct Solver {
     trace("init: D=%lld q=%d nev=%d max_basis=%d keep=%d", (long long)D, q, nev, mb, ls);
     TRY(random_block<T>(W, q, D, q, q, 0, p->seed, s));
     int ndef = 0;
-    TRY(cholqr2(W, 0.0, 1e-8, &ndef));
-    if (ndef) return fail(TRBL_ERR_BREAKDOWN, "start block is rank deficient (q > D?)");
+    TRY(cholqr2(W, 0.0, 1e-8, tau_max, &ndef));
+    if (ndef) TRY(column_qr(0));
     TRY(copy_cols<T, T>(Vk, q, basis, mb, D, q, s));
     nb = q;
     return TRBL_OK;
@@ -460,6 +513,8 @@ struct Solver {
     ms_qr += tm.ms(2, 3);
     ms_ritz += tm.ms(3, 4);
     ms_restart += tm.ms(4, 5);
+    trace("step %d phases ms: apply %.2f orth %.2f qr %.2f ritz %.2f restart %.2f", iter, tm.ms(0, 1), tm.ms(1, 2),
+          tm.ms(2, 3), tm.ms(3, 4), tm.ms(4, 5));
     return TRBL_OK;
   }
 
@@ -535,6 +590,7 @@ struct Solver {
     mb = p->max_basis;
     dtype = std::is_same<T, double>::value ? TRBL_F64 : TRBL_F32;
     tau = dtype == TRBL_F64 ? 1e-10 : 1e-4;
+    tau_max = dtype == TRBL_F64 ? 1e-6 : 1e-3;
     if (q < 1 || q > 64) return fail(TRBL_ERR_ARG, "q=%d outside [1, 64]", q);
     if (nev < 1) return fail(TRBL_ERR_ARG, "nev must be positive");
     if (mb > D) return fail(TRBL_ERR_ARG, "max_basis=%d exceeds the dimension %lld", mb, (long long)D);
@@ -609,8 +665,19 @@ struct Solver {
       }
     }
     TRBL_CUDA(cudaMemsetAsync(Tm, 0, sizeof(double) * mb * mb, s));
-    TRBL_CUDA(cudaMallocHost(&hbuf, sizeof(double) * (2 * mb) + sizeof(int) * kFlagInts));
-    hflags = reinterpret_cast<int*>(hbuf + 2 * mb);
+    const size_t nh = size_t(2) * mb + size_t(q) * q;  // Ritz values, residuals / a q x q Gram
+    TRBL_CUDA(cudaMallocHost(&hbuf, sizeof(double) * nh + sizeof(int) * kFlagInts));
+    hflags = reinterpret_cast<int*>(hbuf + nh);
+    // The eigensolver loads size-dependent kernel variants on first use,
+    // which can take seconds; run it once per size class here so that the
+    // iteration does not pay it.
+    for (int n = q; n <= mb; n = (n < mb && 2 * n > mb) ? mb : 2 * n) {
+      TRBL_CUDA(cudaMemsetAsync(Aw, 0, sizeof(double) * size_t(mb) * n, s));
+      TRBL_SOLVER(cusolverDnDsyevd(sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, Aw, mb, theta,
+                                   syev_work, lwork, devinfo));
+      if (n == mb) break;
+    }
+    TRBL_CUDA(cudaStreamSynchronize(s));
     return TRBL_OK;
   }
 };
