@@ -133,6 +133,21 @@ void trbl_hamiltonian_destroy(trbl_hamiltonian* h);
 int trbl_apply_block(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, int64_t ldw,
                      int q, int dtype, void* stream);
 
+/* C = B^T W: the m x q projection coefficients of a block W (D x q) on m
+ * stored vectors B (D x m), the product "alpha_k := V_k^T W" of Alg. 3/4 and
+ * the coefficients of the reorthogonalisation against the Krylov basis
+ * (Sec. III C/D).  B and W are device arrays of element type dtype
+ * (TRBL_F32 or TRBL_F64), row-major with leading dimensions ldb >= m,
+ * ldw >= q; C is a device FP64 array, row-major m x q (leading dimension
+ * q), overwritten.  Products are summed in dtype inside fixed row chunks and
+ * the chunk sums are added in FP64 in a fixed order (bit-reproducible for
+ * given sizes).  1 <= q <= 64, m >= 1.  The partial-sum scratch
+ * (chunks x m x q doubles) is taken with cudaMallocAsync and released with
+ * cudaFreeAsync on the stream.  Asynchronous on stream.  Errors:
+ * TRBL_ERR_ARG, TRBL_ERR_OOM, TRBL_ERR_CUDA. */
+int trbl_block_dot(const void* B, int64_t ldb, int m, const void* W, int64_t ldw, int q, int64_t D,
+                   int dtype, double* C, void* stream);
+
 #define TRBL_PREC_F64 1   /* FP64 vectors, apply and projections */
 #define TRBL_PREC_MIXED 2 /* FP32 vectors and apply; FP64 CGS2 coefficients, CholQR2, Ritz */
 

@@ -81,6 +81,7 @@ def lib():
         "trbl_solver_stats": (C.c_int, [_VP, C.POINTER(trbl_stats)]),
         "trbl_solver_finish": (C.c_int, [_VP, _DP, _DP, _VP, C.POINTER(trbl_stats)]),
         "trbl_solver_destroy": (None, [_VP]),
+        "trbl_block_dot": (C.c_int, [_VP, C.c_int64, C.c_int, _VP, C.c_int64, C.c_int, C.c_int64, C.c_int, _VP, _VP]),
         "trbl_kernel_launches": (C.c_longlong, []),
         "trbl_last_error": (C.c_char_p, []),
     }
@@ -179,6 +180,25 @@ def trbl_hamiltonian_destroy(h: int):
 def trbl_apply_block(h: int, V_ptr: int, ldv: int, W_ptr: int, ldw: int, q: int, dtype: int,
                      stream: int = 0):
     _check(lib().trbl_apply_block(h, V_ptr, int(ldv), W_ptr, int(ldw), int(q), int(dtype), stream))
+
+
+def trbl_block_dot(B_ptr: int, ldb: int, m: int, W_ptr: int, ldw: int, q: int, D: int, dtype: int,
+                   C_ptr: int, stream: int = 0):
+    _check(lib().trbl_block_dot(B_ptr, int(ldb), int(m), W_ptr, int(ldw), int(q), int(D), int(dtype), C_ptr,
+                                stream))
+
+
+def block_dot(B, W, stream=None):
+    """C = B^T W (FP64, m x q) for torch CUDA tensors B (D x m) and W (D x q)."""
+    import torch
+    if B.dtype != W.dtype or B.stride(1) != 1 or W.stride(1) != 1 or B.shape[0] != W.shape[0]:
+        raise ValueError("B and W must share dtype and rows, with unit column stride")
+    dt = TRBL_F64 if B.dtype == torch.float64 else TRBL_F32
+    C = torch.empty((B.shape[1], W.shape[1]), dtype=torch.float64, device=B.device)
+    s = stream if stream is not None else torch.cuda.current_stream(B.device)
+    trbl_block_dot(B.data_ptr(), B.stride(0), B.shape[1], W.data_ptr(), W.stride(0), W.shape[1], B.shape[0], dt,
+                   C.data_ptr(), s.cuda_stream)
+    return C
 
 
 def trbl_solve(h: int, params: trbl_params, evals_ptr, resid_ptr, evecs_ptr: int,

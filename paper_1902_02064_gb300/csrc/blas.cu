@@ -312,7 +312,47 @@ int dot_launch(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, i
   return TRBL_OK;
 }
 
+template <typename T, int QP>
+int dot_launch_capped(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, int64_t D, double* C,
+                      double* partial, size_t partial_bytes, int sm_count, cudaStream_t s) {
+  constexpr int RS = DotCfg<T>::RS;
+  const int mtiles = (m + MT - 1) / MT;
+  const size_t per_chunk = size_t(m) * q * sizeof(double);
+  const int64_t fit = int64_t(partial_bytes / per_chunk);
+  if (fit < 1) return fail(TRBL_ERR_ARG, "block_dot: m*q = %lld exceeds the partial-sum buffer", (long long)m * q);
+  int64_t nchunk = (4 * sm_count + mtiles - 1) / mtiles;
+  const int64_t max_chunks = (D + RS - 1) / RS;
+  nchunk = std::max<int64_t>(1, std::min(std::min(nchunk, max_chunks), fit));
+  int64_t rows = (D + nchunk - 1) / nchunk;
+  rows = (rows + RS - 1) / RS * RS;
+  nchunk = (D + rows - 1) / rows;
+  dim3 grid(mtiles, unsigned(nchunk));
+  block_dot_kernel<T, QP><<<grid, 32 * (QP / 4), 0, s>>>(B, ldb, m, W, ldw, q, D, rows, partial); note_launch();
+  TRBL_CUDA(cudaGetLastError());
+  const int mq = m * q;
+  reduce_partials_kernel<<<(mq + 255) / 256, 256, 0, s>>>(partial, int(nchunk), mq, C); note_launch();
+  TRBL_CUDA(cudaGetLastError());
+  return TRBL_OK;
+}
+
 }  // namespace
+
+template <typename T>
+int block_dot_capped(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, int64_t D, double* C,
+                     double* partial, size_t partial_bytes, int sm_count, cudaStream_t s) {
+  if (m <= 0 || D <= 0) return fail(TRBL_ERR_ARG, "block_dot: empty operand");
+  if (q <= 4) return dot_launch_capped<T, 4>(B, ldb, m, W, ldw, q, D, C, partial, partial_bytes, sm_count, s);
+  if (q <= 8) return dot_launch_capped<T, 8>(B, ldb, m, W, ldw, q, D, C, partial, partial_bytes, sm_count, s);
+  if (q <= 16) return dot_launch_capped<T, 16>(B, ldb, m, W, ldw, q, D, C, partial, partial_bytes, sm_count, s);
+  if (q <= 32) return dot_launch_capped<T, 32>(B, ldb, m, W, ldw, q, D, C, partial, partial_bytes, sm_count, s);
+  if (q <= 64) return dot_launch_capped<T, 64>(B, ldb, m, W, ldw, q, D, C, partial, partial_bytes, sm_count, s);
+  return fail(TRBL_ERR_ARG, "block_dot: q=%d > 64", q);
+}
+
+template int block_dot_capped<float>(const float*, int64_t, int, const float*, int64_t, int, int64_t, double*,
+                                     double*, size_t, int, cudaStream_t);
+template int block_dot_capped<double>(const double*, int64_t, int, const double*, int64_t, int, int64_t, double*,
+                                      double*, size_t, int, cudaStream_t);
 
 size_t block_dot_workspace_bytes(int m, int q, int sm_count) {
   const int mtiles = (m + MT - 1) / MT;

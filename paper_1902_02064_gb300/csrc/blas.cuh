@@ -20,6 +20,13 @@ template <typename T>
 int block_dot(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, int64_t D, double* C,
               Workspace& ws, cudaStream_t s);
 
+// block_dot with a caller-given partial-sum buffer of partial_bytes: the
+// number of row chunks is capped so that chunks * m * q doubles fit.
+// TRBL_ERR_ARG when even one chunk does not fit.
+template <typename T>
+int block_dot_capped(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, int64_t D, double* C,
+                     double* partial, size_t partial_bytes, int sm_count, cudaStream_t s);
+
 // Out[:, 0:n] = alpha * In[:, 0:K] U[K x n] + beta * Out (U FP64 row-major, ld ldu).
 // In and Out must not overlap.
 template <typename T>

@@ -1,0 +1,45 @@
+"""Parity of trbl_block_dot (C = B^T W, the block projection of Alg. 3/4 and
+of the reorthogonalisation, Sec. III C/D) with numpy in FP64.
+
+Tolerance: |C - B^T W|_ij <= rtol * (|B|^T |W|)_ij with rtol = 1e-12 for
+FP64 data and 1e-5 for FP32 data (FP32 products summed in FP32 inside row
+chunks, chunk sums in FP64)."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+trbl = pytest.importorskip("paper_1902_02064_gb300")
+
+pytestmark = pytest.mark.gpu
+RTOL = {torch.float64: 1e-12, torch.float32: 1e-5}
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("D,m,q", [(1, 1, 1), (1000, 7, 3), (33333, 130, 32), (200001, 300, 16), (5000, 64, 64)])
+def test_block_dot_matches_numpy(dtype, D, m, q):
+    B = synth.random_block(D, m, 11)
+    W = synth.random_block(D, q, 12)
+    Bt = torch.from_numpy(B).to(dtype)
+    Wt = torch.from_numpy(W).to(dtype)
+    C = trbl.block_dot(Bt.cuda(), Wt.cuda()).cpu().numpy()
+    Bd, Wd = Bt.double().numpy(), Wt.double().numpy()
+    ref = Bd.T @ Wd
+    bound = np.abs(Bd).T @ np.abs(Wd)
+    assert np.all(np.abs(C - ref) <= RTOL[dtype] * bound + 1e-300)
+
+
+def test_block_dot_strided_and_errors():
+    D, m, q = 4097, 40, 8
+    big = torch.from_numpy(synth.random_block(D, 64, 3)).cuda()
+    B = big[:, 5:5 + m]
+    W = big[:, 50:50 + q]
+    C = trbl.block_dot(B, W)
+    ref = B.cpu().numpy().T @ W.cpu().numpy()
+    assert np.allclose(C.cpu().numpy(), ref, rtol=0, atol=1e-11)
+    with pytest.raises(trbl.TrblError):
+        trbl.trbl_block_dot(B.data_ptr(), 64, m, W.data_ptr(), 64, 65, D, trbl.TRBL_F64, C.data_ptr(), 0)
+    host = np.zeros((D, q))
+    with pytest.raises(trbl.TrblError):
+        trbl.trbl_block_dot(B.data_ptr(), 64, m, host.ctypes.data, q, q, D, trbl.TRBL_F64, C.data_ptr(), 0)
