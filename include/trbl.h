@@ -148,6 +148,31 @@ int trbl_apply_block(const trbl_hamiltonian* h, const void* V, int64_t ldv, void
 int trbl_block_dot(const void* B, int64_t ldb, int m, const void* W, int64_t ldw, int q, int64_t D,
                    int dtype, double* C, void* stream);
 
+/* Allocation-free form of trbl_block_dot, for callers that must not
+ * allocate device memory during the call: code running where the CUDA
+ * allocator may not be entered (inside host callbacks, or while another
+ * component owns and budgets all device memory) and latency-critical loops
+ * that cannot afford an allocation's implicit synchronisation.  The paper
+ * has no counterpart; it is a service of this library.
+ *
+ * Same arguments, layouts, arithmetic and errors as trbl_block_dot, except
+ * that the partial-sum scratch is a fixed array compiled into the library
+ * (TRBL_NOALLOC_SCRATCH_BYTES per device, held by every device that loads
+ * the library until the process exits).  It calls no cudaMalloc, cudaFree
+ * or allocating library routine.  m * q * 8 must not exceed
+ * TRBL_NOALLOC_SCRATCH_BYTES (TRBL_ERR_ARG otherwise); larger products use
+ * fewer row chunks, never more scratch.
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (with that device current); make that first call before any stream
+ * capture.  All calls on a device share the one array: calls whose
+ * executions overlap on the GPU (different streams, or different host
+ * threads) race and give wrong results.  Every call overwrites the part of
+ * the scratch it reads, so no clearing is needed between calls. */
+#define TRBL_NOALLOC_SCRATCH_BYTES (8u << 20)
+int trbl_block_dot_noalloc(const void* B, int64_t ldb, int m, const void* W, int64_t ldw, int q, int64_t D,
+                           int dtype, double* C, void* stream);
+
 #define TRBL_PREC_F64 1   /* FP64 vectors, apply and projections */
 #define TRBL_PREC_MIXED 2 /* FP32 vectors and apply; FP64 CGS2 coefficients, CholQR2, Ritz */
 

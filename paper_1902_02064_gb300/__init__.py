@@ -17,6 +17,7 @@ from ._lib import (  # noqa: F401
     trbl_basis_create, trbl_basis_destroy, trbl_basis_info, trbl_basis_export,
     trbl_basis_export_jumps, trbl_hamiltonian_create, trbl_hamiltonian_destroy,
     trbl_apply_block, trbl_solve, trbl_last_error, trbl_kernel_launches, trbl_block_dot, block_dot,
+    trbl_block_dot_noalloc,
     trbl_solver_create, trbl_solver_step, trbl_solver_step_host, trbl_solver_block,
     trbl_solver_stats, trbl_solver_destroy,
     Basis, Hamiltonian, Solver, solve,

@@ -82,6 +82,8 @@ def lib():
         "trbl_solver_finish": (C.c_int, [_VP, _DP, _DP, _VP, C.POINTER(trbl_stats)]),
         "trbl_solver_destroy": (None, [_VP]),
         "trbl_block_dot": (C.c_int, [_VP, C.c_int64, C.c_int, _VP, C.c_int64, C.c_int, C.c_int64, C.c_int, _VP, _VP]),
+        "trbl_block_dot_noalloc": (C.c_int, [_VP, C.c_int64, C.c_int, _VP, C.c_int64, C.c_int, C.c_int64, C.c_int,
+                                             _VP, _VP]),
         "trbl_kernel_launches": (C.c_longlong, []),
         "trbl_last_error": (C.c_char_p, []),
     }
@@ -186,6 +188,14 @@ def trbl_block_dot(B_ptr: int, ldb: int, m: int, W_ptr: int, ldw: int, q: int, D
                    C_ptr: int, stream: int = 0):
     _check(lib().trbl_block_dot(B_ptr, int(ldb), int(m), W_ptr, int(ldw), int(q), int(D), int(dtype), C_ptr,
                                 stream))
+
+
+def trbl_block_dot_noalloc(B_ptr: int, ldb: int, m: int, W_ptr: int, ldw: int, q: int, D: int, dtype: int,
+                           C_ptr: int, stream: int = 0):
+    """Allocation-free C = B^T W (see include/trbl.h): scratch is a fixed
+    array compiled into the library; overlapping calls on one device race."""
+    _check(lib().trbl_block_dot_noalloc(B_ptr, int(ldb), int(m), W_ptr, int(ldw), int(q), int(D), int(dtype),
+                                        C_ptr, stream))
 
 
 def block_dot(B, W, stream=None):
