@@ -10,6 +10,7 @@
 // thread block, and the per-block partial sums are reduced across blocks in
 // FP64 in a fixed order (deterministic).
 #include <algorithm>
+#include <type_traits>
 
 #include "blas.cuh"
 
@@ -396,6 +397,12 @@ int rowgemm(const T* In, int64_t ldi, int K, const double* U, int64_t ldu, int n
   if (K <= 0) {
     // Out = beta * Out
     if (beta == 1.0) return TRBL_OK;
+  }
+  if constexpr (std::is_same<T, float>::value) {
+    if (K > 0 && n <= 32) {
+      const int rc = rowgemm_tma(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta, s);
+      if (rc != -1) return rc;
+    }
   }
   if (K > 0 && n <= 64) {
     const int NP = n <= 16 ? 16 : (n <= 32 ? 32 : 64);

@@ -33,6 +33,13 @@ template <typename T>
 int rowgemm(const T* In, int64_t ldi, int K, const double* U, int64_t ldu, int n, T* Out,
             int64_t ldo, int64_t D, double alpha, double beta, cudaStream_t s);
 
+// FP32 Out = alpha * In U + beta * Out (n <= 32) with In streamed by TMA
+// (rowgemm_tma.cu); -1 when the shapes or alignment do not allow it.
+int rowgemm_tma(const float* In, int64_t ldi, int K, const double* U, int64_t ldu, int n, float* Out, int64_t ldo,
+                int64_t D, double alpha, double beta, cudaStream_t s);
+// Enqueues a copy of the TMA-wait timeout word (0 = none) to host memory.
+int tma_error_to_host(int* host, cudaStream_t s);
+
 // dst[:, 0:ncol] = src[:, 0:ncol] (with type conversion).
 template <typename S, typename T>
 int copy_cols(const S* src, int64_t lds, T* dst, int64_t ldd, int64_t D, int ncol, cudaStream_t s);

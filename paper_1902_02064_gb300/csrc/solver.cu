@@ -212,6 +212,7 @@ __global__ void resid_final_kernel(const double* __restrict__ part, int nchunk, 
 constexpr int kF1 = 0;     // pass-1 Cholesky: count, then one flag per column
 constexpr int kF2 = 80;    // pass-2 Cholesky
 constexpr int kInfo = 160; // syevd info
+constexpr int kTmaErr = 170;  // TMA wait timeout word
 constexpr int kFlagInts = 192;
 
 // Host-side progress trace, on when the environment sets TRBL_TRACE=1.
@@ -332,7 +333,9 @@ struct Solver {
     TRY(rowgemm<T>(W2, q, q, R2i, q, q, Vk, q, D, 1.0, 0.0, s));
     upper_mul_kernel<<<(q * q + 127) / 128, 128, 0, s>>>(R2, R1, q, beta); note_launch();
     TRBL_CUDA(cudaGetLastError());
+    TRY(tma_error_to_host(hflags + kTmaErr, s));
     TRBL_CUDA(cudaStreamSynchronize(s));
+    if (hflags[kTmaErr]) return fail(TRBL_ERR_CUDA, "a TMA wait in the basis update timed out");
     *ndef = hflags[kF1] + hflags[kF2];
     return TRBL_OK;
   }
