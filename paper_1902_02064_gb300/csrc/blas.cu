@@ -338,6 +338,10 @@ int dot_launch_capped(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, i
 
 }  // namespace
 
+void reduce_partials(const double* partial, int nchunk, int mq, double* C, cudaStream_t s) {
+  reduce_partials_kernel<<<(mq + 255) / 256, 256, 0, s>>>(partial, nchunk, mq, C); note_launch();
+}
+
 template <typename T>
 int block_dot_capped(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, int64_t D, double* C,
                      double* partial, size_t partial_bytes, int sm_count, cudaStream_t s) {
@@ -365,6 +369,10 @@ template <typename T>
 int block_dot(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, int64_t D, double* C,
               Workspace& ws, cudaStream_t s) {
   if (m <= 0) return TRBL_OK;
+  if constexpr (std::is_same<T, float>::value) {
+    const int rc = block_dot_tma(B, ldb, m, W, ldw, q, D, C, ws.partial, ws.partial_bytes, ws.sm_count, s);
+    if (rc != -1) return rc;
+  }
   if (q <= 4) return dot_launch<T, 4>(B, ldb, m, W, ldw, q, D, C, ws, s);
   if (q <= 8) return dot_launch<T, 8>(B, ldb, m, W, ldw, q, D, C, ws, s);
   if (q <= 16) return dot_launch<T, 16>(B, ldb, m, W, ldw, q, D, C, ws, s);

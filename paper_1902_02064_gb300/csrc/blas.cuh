@@ -39,6 +39,11 @@ int rowgemm_tma(const float* In, int64_t ldi, int K, const double* U, int64_t ld
                 int64_t D, double alpha, double beta, cudaStream_t s);
 // Enqueues a copy of the TMA-wait timeout word (0 = none) to host memory.
 int tma_error_to_host(int* host, cudaStream_t s);
+// FP32 C = B^T W (q <= 32) with TMA-streamed operands (dot_tma.cu); -1 when
+// the shapes or alignment do not allow it.
+int block_dot_tma(const float* B, int64_t ldb, int m, const float* W, int64_t ldw, int q, int64_t D, double* C,
+                  double* partial, size_t partial_bytes, int sm_count, cudaStream_t s);
+int dot_error_to_host(int* host, cudaStream_t s);
 
 // dst[:, 0:ncol] = src[:, 0:ncol] (with type conversion).
 template <typename S, typename T>

@@ -334,8 +334,9 @@ struct Solver {
     upper_mul_kernel<<<(q * q + 127) / 128, 128, 0, s>>>(R2, R1, q, beta); note_launch();
     TRBL_CUDA(cudaGetLastError());
     TRY(tma_error_to_host(hflags + kTmaErr, s));
+    TRY(dot_error_to_host(hflags + kTmaErr + 1, s));
     TRBL_CUDA(cudaStreamSynchronize(s));
-    if (hflags[kTmaErr]) return fail(TRBL_ERR_CUDA, "a TMA wait in the basis update timed out");
+    if (hflags[kTmaErr] || hflags[kTmaErr + 1]) return fail(TRBL_ERR_CUDA, "a TMA wait in a projection timed out");
     *ndef = hflags[kF1] + hflags[kF2];
     return TRBL_OK;
   }
