@@ -148,6 +148,28 @@ int trbl_apply_block(const trbl_hamiltonian* h, const void* V, int64_t ldv, void
 int trbl_block_dot(const void* B, int64_t ldb, int m, const void* W, int64_t ldw, int q, int64_t D,
                    int dtype, double* C, void* stream);
 
+/* Number of independent parameters of H on these spaces, in the canonical
+ * order used by trbl_grad: one-body A (a <= c with equal 2m, a-major), one-body
+ * B, two-body AA (pairs I = (i<j) lexicographic, J >= I with equal pair 2m),
+ * BB, then AB (pairs (a, b) a-major, J >= I with equal pair 2m).  A
+ * parameter at slot (I, J) with I != J sets both V_IJ and V_JI. */
+int trbl_param_count(const trbl_basis* b, int64_t* n);
+
+/* Hellmann-Feynman gradient (Sec. II: H is linear in its parameters, so
+ * dE_k/dtheta = <x_k| dH/dtheta |x_k> for a normalised eigenvector x_k):
+ * dtheta[p] = sum over the nvec given vectors of <x| dH/dtheta_p |x>, for
+ * every parameter in trbl_param_count's order.  For a cluster of
+ * (near-)degenerate levels pass the whole cluster: the sum is the derivative
+ * of the cluster's eigenvalue sum, Tr(P_C dH/dtheta).  X: device, D x nvec
+ * row-major (ld ldx), dtype TRBL_F32 or TRBL_F64, 1 <= nvec <= 32;
+ * dtheta: host FP64 [nparams].  The elements visited are those of the block
+ * product (App. B); bins are summed with FP64 atomics.  The first call
+ * builds device tables kept with the Hamiltonian.  Synchronises the stream.
+ * Errors: TRBL_ERR_ARG (including nparams != trbl_param_count),
+ * TRBL_ERR_OOM, TRBL_ERR_CUDA. */
+int trbl_grad(const trbl_hamiltonian* h, const void* X, int64_t ldx, int nvec, int dtype, double* dtheta,
+              int64_t nparams, void* stream);
+
 /* Allocation-free form of trbl_block_dot, for callers that must not
  * allocate device memory during the call: code running where the CUDA
  * allocator may not be entered (inside host callbacks, or while another

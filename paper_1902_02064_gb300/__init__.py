@@ -20,5 +20,6 @@ from ._lib import (  # noqa: F401
     trbl_block_dot_noalloc,
     trbl_solver_create, trbl_solver_step, trbl_solver_step_host, trbl_solver_block,
     trbl_solver_stats, trbl_solver_destroy,
+    trbl_param_count, trbl_grad, arrays_from_theta, clusters_of, hf_gradient, LowestEigenvalues,
     Basis, Hamiltonian, Solver, solve,
 )

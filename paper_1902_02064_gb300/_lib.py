@@ -84,6 +84,8 @@ def lib():
         "trbl_block_dot": (C.c_int, [_VP, C.c_int64, C.c_int, _VP, C.c_int64, C.c_int, C.c_int64, C.c_int, _VP, _VP]),
         "trbl_block_dot_noalloc": (C.c_int, [_VP, C.c_int64, C.c_int, _VP, C.c_int64, C.c_int, C.c_int64, C.c_int,
                                              _VP, _VP]),
+        "trbl_param_count": (C.c_int, [_VP, C.POINTER(C.c_int64)]),
+        "trbl_grad": (C.c_int, [_VP, _VP, C.c_int64, C.c_int, C.c_int, _DP, C.c_int64, _VP]),
         "trbl_kernel_launches": (C.c_longlong, []),
         "trbl_last_error": (C.c_char_p, []),
     }
@@ -225,6 +227,7 @@ class Basis:
     def __init__(self, spaceA, kA: int, spaceB, kB: int, twoM: int):
         self.handle = None
         self.handle = trbl_basis_create(spaceA, kA, spaceB, kB, twoM)
+        self.twomA, self.twomB = tuple(int(x) for x in spaceA.twom), tuple(int(x) for x in spaceB.twom)
         self.info = trbl_basis_info(self.handle)
         self.dim = self.info["dim"]
 
@@ -398,3 +401,132 @@ class Solver:
         if getattr(self, "handle", None) and _LIB is not None:
             _LIB.trbl_solver_destroy(self.handle)
             self.handle = None
+
+
+# ---- Hellmann-Feynman gradient -------------------------------------------------
+
+def trbl_param_count(b: int) -> int:
+    n = C.c_int64()
+    _check(lib().trbl_param_count(b, C.byref(n)))
+    return n.value
+
+
+def trbl_grad(h: int, X_ptr: int, ldx: int, nvec: int, dtype: int, out: np.ndarray, stream: int = 0):
+    _check(lib().trbl_grad(h, X_ptr, int(ldx), int(nvec), int(dtype), out.ctypes.data_as(_DP), int(out.size),
+                           stream))
+
+
+def _canonical_params(twomA, twomB):
+    """(kind, indices) of every parameter in trbl_param_count's order."""
+    out = []
+    for name, m in (("h1A", twomA), ("h1B", twomB)):
+        n = len(m)
+        for a in range(n):
+            for c in range(a, n):
+                if m[a] == m[c]:
+                    out.append((name, (a, c)))
+    for name, m in (("VAA", twomA), ("VBB", twomB)):
+        n = len(m)
+        pairs = [(i, j) for i in range(n) for j in range(i + 1, n)]
+        for I in range(len(pairs)):
+            for J in range(I, len(pairs)):
+                (i, j), (k, l) = pairs[I], pairs[J]
+                if m[i] + m[j] == m[k] + m[l]:
+                    out.append((name, (i, j, k, l)))
+    nB = len(twomB)
+    pairs = [(a, b) for a in range(len(twomA)) for b in range(nB)]
+    for I in range(len(pairs)):
+        for J in range(I, len(pairs)):
+            (a, b), (c, d) = pairs[I], pairs[J]
+            if twomA[a] + twomB[b] == twomA[c] + twomB[d]:
+                out.append(("VAB", (a, b, c, d)))
+    return out
+
+
+def arrays_from_theta(twomA, twomB, theta):
+    """Dense coefficient arrays (h1A, h1B, VAA, VBB, VAB) of trbl_hamiltonian_create
+    from a parameter vector in trbl_param_count's order."""
+    nA, nB = len(twomA), len(twomB)
+    A = {"h1A": np.zeros((nA, nA)), "h1B": np.zeros((nB, nB)), "VAA": np.zeros((nA,) * 4),
+         "VBB": np.zeros((nB,) * 4), "VAB": np.zeros((nA, nB, nA, nB))}
+    theta = np.asarray(theta, dtype=np.float64)
+    params = _canonical_params(twomA, twomB)
+    if len(params) != theta.size:
+        raise ValueError("theta has %d entries, the spaces have %d parameters" % (theta.size, len(params)))
+    for (name, ix), x in zip(params, theta):
+        T = A[name]
+        if len(ix) == 2:
+            T[ix[0], ix[1]] = x
+            T[ix[1], ix[0]] = x
+        else:
+            i, j, k, l = ix
+            T[i, j, k, l] = x
+            T[k, l, i, j] = x
+    return A["h1A"], A["h1B"], A["VAA"], A["VBB"], A["VAB"]
+
+
+def clusters_of(evals, gap):
+    """Index lists of consecutive eigenvalues closer than gap."""
+    out, cur = [], [0]
+    for k in range(1, len(evals)):
+        if evals[k] - evals[k - 1] < gap:
+            cur.append(k)
+        else:
+            out.append(cur)
+            cur = [k]
+    out.append(cur)
+    return out
+
+
+def hf_gradient(h: "Hamiltonian", X, cols=None, stream=None) -> np.ndarray:
+    """sum over the selected columns x of X of <x| dH/dtheta |x> (trbl_grad),
+    in chunks of at most 32 columns."""
+    import torch
+    if cols is None:
+        cols = list(range(X.shape[1]))
+    dt = TRBL_F64 if X.dtype == torch.float64 else TRBL_F32
+    n = trbl_param_count(h.basis.handle)
+    total = np.zeros(n)
+    part = np.zeros(n)
+    s = stream if stream is not None else torch.cuda.current_stream(X.device)
+    for c0 in range(0, len(cols), 32):
+        sub = X[:, cols[c0:c0 + 32]].contiguous()
+        trbl_grad(h.handle, sub.data_ptr(), sub.stride(0), sub.shape[1], dt, part, s.cuda_stream)
+        total += part
+    return total
+
+
+class LowestEigenvalues:
+    """torch.autograd.Function computing the nev lowest eigenvalues of H(theta)
+    with trbl_solve and their Hellmann-Feynman gradient with trbl_grad.
+
+    Within a cluster of levels closer than cluster_tol * ||H|| only the sum of
+    the derivatives is defined; backward gives each member the cluster's mean
+    derivative (exact for losses symmetric within a cluster)."""
+
+    @staticmethod
+    def apply(theta, basis, nev, q, max_basis, tol, precision=TRBL_PREC_F64, cluster_tol=1e-8, seed=1):
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, th):
+                b = basis
+                twomA, twomB = b.twomA, b.twomB
+                h = Hamiltonian(b, *arrays_from_theta(twomA, twomB, th.detach().cpu().numpy()))
+                ev, rs, X, st = solve(h, nev, q, max_basis, tol, precision=precision, seed=seed)
+                cl = clusters_of(ev, cluster_tol * max(st["normH"], 1e-300))
+                G = np.zeros((nev, th.numel()))
+                for c in cl:
+                    g = hf_gradient(h, X, c) / len(c)
+                    for k in c:
+                        G[k] = g
+                ctx.save_for_backward(torch.from_numpy(G).to(th.dtype))
+                return torch.from_numpy(ev).to(th.dtype)
+
+            @staticmethod
+            def backward(ctx, gout):
+                (G,) = ctx.saved_tensors
+                return gout @ G
+
+        return _Fn.apply(theta)

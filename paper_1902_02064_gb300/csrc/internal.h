@@ -117,8 +117,12 @@ struct trbl_hamiltonian {
   trbl::DevG<double> g64;
   trbl::DevG<float> g32;
   void* garena = nullptr;
+  void* grad = nullptr;  // gradient tables, built on the first trbl_grad call
   size_t arena_bytes = 0;
 };
+
+// Frees the gradient tables of a Hamiltonian (grad.cu).
+void trbl_grad_state_free(void* g);
 
 namespace trbl {
 // Uploads the tables of h to the current device (apply.cu).

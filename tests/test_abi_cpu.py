@@ -87,3 +87,14 @@ def test_errors_are_reported():
     assert "n_particles" in str(e.value)
     with pytest.raises(trbl.TrblError):
         trbl.Basis(sp, 2, sp, 2, 41)  # no determinants reach 2M = 41
+
+
+def test_parameter_order_matches_generator():
+    for shells in (synth.SPACE12_SHELLS, synth.SPACE20_SHELLS, synth.TABLE1_SHELLS):
+        sp = synth.make_space(shells)
+        inter = synth.draw_interaction(sp, sp, 9)
+        b = trbl.Basis(sp, 1, sp, 1, sp.twom[0] + sp.twom[-1])
+        assert trbl.trbl_param_count(b.handle) == len(inter.theta)
+        arrs = trbl.arrays_from_theta(sp.twom, sp.twom, inter.theta)
+        for a, r in zip(arrs, (inter.h1A, inter.h1B, inter.VAA, inter.VBB, inter.VAB)):
+            assert np.array_equal(a, r)
