@@ -374,6 +374,8 @@ def run_ours(args, rank, world):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes, "ms_per_step": el / args.steps * 1e3},
     }
+    if rank == 0 and world == 1 and not args.no_ttn:
+        line["time_to_nev"] = time_to_nev(trbl)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, q, args.cpu_seconds)
     del sv
@@ -381,6 +383,35 @@ def run_ours(args, rank, world):
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def time_to_nev(trbl, name="s12_4p4n"):
+    """Full solves of the 12-m-state 4+4 workload (D = 28,503, nev = 100):
+    mixed precision q = 8, FP64 q = 8, and plain FP64 Lanczos (q = 1), same
+    GPU; eigenvalue errors against the oracle's stored eigenvalues."""
+    import torch
+    w, sa, sb, inter = synth.workload(name)
+    tb = trbl.Basis(sa, w.nA, sb, w.nB, w.twoM)
+    th = trbl.Hamiltonian.from_interaction(tb, inter)
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "eigs_%s.json" % name)))
+    ref = np.array(gold["evals"][: w.nev])
+    normH = gold["normH"]
+    out = {"workload": name, "dim": tb.dim, "nev": w.nev, "max_basis": w.max_basis, "normH": normH}
+    runs = (("mixed_q8", trbl.TRBL_PREC_MIXED, w.q, 1e-6), ("fp64_q8", trbl.TRBL_PREC_F64, w.q, 1e-10),
+            ("fp64_q1", trbl.TRBL_PREC_F64, 1, 1e-10))
+    for label, prec, q, tol in runs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev, rs, X, st = trbl.solve(th, w.nev, q, w.max_basis, tol, precision=prec, want_vectors=False,
+                                   raise_on_noconv=False, max_iter=20000)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        out[label] = {"seconds": el, "tol_rel_normH": tol, "converged": st["converged"], "rc": st["rc"],
+                      "iterations": st["iterations"], "restarts": st["restarts"],
+                      "max_abs_eig_err_over_normH": float(np.abs(ev - ref).max() / normH),
+                      "max_true_resid_over_normH": float(np.nanmax(rs) / normH),
+                      "phase_ms": {k: st[k] for k in ("ms_apply", "ms_orth", "ms_qr", "ms_ritz", "ms_restart")}}
+    return out
 
 
 def run_apply_only(args):
@@ -428,6 +459,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ttn", action="store_true", help="skip the time-to-nev solves")
     ap.add_argument("--apply-only", default=None, help="time only W = H V on this workload")
     ap.add_argument("--workload", default=WORKLOAD, help="workload of the solver steps (default: the 5+5 space)")
     ap.add_argument("--q", type=int, default=0)

@@ -208,7 +208,8 @@ typedef struct trbl_params {
   double tol;          /* converged when ||beta_k U_{last q rows,i}|| <= tol * ||H|| for i < nev */
   int precision;       /* TRBL_PREC_F64 or TRBL_PREC_MIXED */
   int max_iter;        /* block iterations cap; 0 = 100000 */
-  int check_every;     /* Rayleigh-Ritz convergence test every this many block steps; 0 = 1 */
+  int check_every;     /* Rayleigh-Ritz convergence test every this many block steps (restarts always
+                          test); 0 = one test per 32 new Lanczos vectors, max(1, 32 / q) steps */
   uint64_t seed;       /* start block: uniform(-1,1) from splitmix64(seed<<32 + i*q + j) */
   double normH;        /* ||H|| used by tol; 0 = estimated by the solver (largest |Ritz value|) */
 } trbl_params;

@@ -462,7 +462,8 @@ struct Solver {
       if (conv_out) *conv_out = conv;
       return TRBL_OK;
     }
-    const int check_every = p->check_every > 0 ? p->check_every : 1;
+    // default cadence: one Rayleigh-Ritz test per 32 new Lanczos vectors
+    const int check_every = p->check_every > 0 ? p->check_every : std::max(1, 32 / q);
     const int max_iter = p->max_iter > 0 ? p->max_iter : 100000;
     trace("iter %d nb %d", iter, nb);
     tm.rec(0, s);
