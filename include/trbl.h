@@ -239,6 +239,28 @@ typedef struct trbl_stats {
 int trbl_solve(const trbl_hamiltonian* h, const trbl_params* p, double* evals, double* resid,
                void* evecs, trbl_stats* stats, void* stream);
 
+/* Batched form of trbl_solve for nset Hamiltonians built on one basis (for
+ * example many parameter sets of one model space), all with the same
+ * parameters p.  One persistent launch of the block product serves every
+ * set; the rest of a block step for all sets is captured into a CUDA graph
+ * per basis size and replayed; Rayleigh-Ritz tests and restarts run between
+ * replays.  Outputs are set-major: evals and resid [nset * nev] (host),
+ * evecs [nset][D x nev] (device, may be NULL), status [nset] (host, per-set
+ * return code, may be NULL); stats summarises the batch.  Needs
+ * q * element size = 16 * 2^i bytes.  A rank-deficient block stops its set
+ * with TRBL_ERR_BREAKDOWN (the column-wise repair of trbl_solve is not
+ * available in batched steps).  Synchronises the stream.  Returns the first
+ * failing set's code, TRBL_OK when all sets finished. */
+int trbl_solve_batch(const trbl_hamiltonian* const* hs, int nset, const trbl_params* p, double* evals,
+                     double* resid, void* evecs, int* status, trbl_stats* stats, void* stream);
+
+/* Times the block product of h at block size q and dtype for the candidate
+ * work-item sizes 32, 64, 128 and 256 neutron rows and keeps the fastest;
+ * ms [4] (host, may be NULL) receives the average time per candidate and
+ * *best_rows the choice.  Allocates two D x q scratch blocks for the timing.
+ * Synchronises the stream. */
+int trbl_apply_autotune(trbl_hamiltonian* h, int q, int dtype, float* ms, int* best_rows, void* stream);
+
 /* Stepwise form of trbl_solve for callers that drive the iteration
  * themselves.  A solver owns its device workspace (basis of D x max_basis
  * vectors plus O(D q) blocks) and runs every call on the stream given here;

@@ -86,6 +86,9 @@ def lib():
                                              _VP, _VP]),
         "trbl_param_count": (C.c_int, [_VP, C.POINTER(C.c_int64)]),
         "trbl_grad": (C.c_int, [_VP, _VP, C.c_int64, C.c_int, C.c_int, _DP, C.c_int64, _VP]),
+        "trbl_solve_batch": (C.c_int, [C.POINTER(_VP), C.c_int, C.POINTER(trbl_params), _DP, _DP, _VP,
+                                       C.POINTER(C.c_int), C.POINTER(trbl_stats), _VP]),
+        "trbl_apply_autotune": (C.c_int, [_VP, C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int), _VP]),
         "trbl_kernel_launches": (C.c_longlong, []),
         "trbl_last_error": (C.c_char_p, []),
     }
@@ -530,3 +533,45 @@ class LowestEigenvalues:
                 return gout @ G
 
         return _Fn.apply(theta)
+
+
+# ---- batched solve and autotuner ---------------------------------------------
+
+def solve_batch(hs, nev: int, q: int, max_basis: int, tol: float, precision: int = TRBL_PREC_F64,
+                keep: int = 0, max_iter: int = 0, check_every: int = 0, seed: int = 1, normH: float = 0.0,
+                want_vectors: bool = False, want_resid: bool = True, stream=None):
+    """trbl_solve_batch over Hamiltonians sharing one basis.  Returns
+    (evals [nset, nev], resid [nset, nev] or None, vectors [nset, D, nev] or
+    None, per-set status, stats dict)."""
+    import torch
+    nset = len(hs)
+    D = hs[0].basis.dim
+    p = _params(nev, q, max_basis, tol, precision, keep, max_iter, check_every, seed, normH)
+    arr = (_VP * nset)(*[h.handle for h in hs])
+    ev = np.zeros((nset, nev))
+    rs = np.zeros((nset, nev)) if want_resid else None
+    status = (C.c_int * nset)()
+    X = None
+    if want_vectors:
+        dt = torch.float64 if precision == TRBL_PREC_F64 else torch.float32
+        X = torch.empty((nset, D, nev), dtype=dt, device="cuda")
+    st = trbl_stats()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib().trbl_solve_batch(arr, nset, C.byref(p), ev.ctypes.data_as(_DP),
+                                rs.ctypes.data_as(_DP) if rs is not None else None,
+                                X.data_ptr() if X is not None else None, status, C.byref(st), s.cuda_stream)
+    d = st.as_dict()
+    d["rc"] = rc
+    d["message"] = trbl_last_error() if rc else ""
+    return ev, rs, X, list(status), d
+
+
+def apply_autotune(h: "Hamiltonian", q: int, dtype: int = TRBL_F32, stream=None):
+    """Times the product for 32/64/128/256 neutron rows per work item and keeps
+    the fastest; returns (times in ms, rows chosen)."""
+    import torch
+    ms = (C.c_float * 4)()
+    best = C.c_int()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().trbl_apply_autotune(h.handle, int(q), int(dtype), ms, C.byref(best), s.cuda_stream))
+    return list(ms), best.value

@@ -75,8 +75,8 @@ __device__ __forceinline__ double flip(double c, int neg) {
 }
 
 template <typename T, int LPE, int CPL>
-__global__ void __launch_bounds__(kThreads) apply_grouped_kernel(DevH<T> h, DevG<T> g, const T* __restrict__ V,
-                                                                 int64_t ldv, T* __restrict__ W, int64_t ldw) {
+__device__ __forceinline__ void grouped_body(const DevH<T>& h, const DevG<T>& g, int item_index,
+                                             const T* __restrict__ V, int64_t ldv, T* __restrict__ W, int64_t ldw) {
   constexpr int VPL = Vec16<T>::N;  // values per 16-byte chunk
   constexpr int G = 32 / LPE;       // element groups per warp
   constexpr int CW = VPL * LPE;     // values covered by one chunk across the group
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kThreads) apply_grouped_kernel(DevH<T> h, DevG
   int* pstart = pj_op + maxP + 1;                             // [ND + 1]
   int* nq = pstart + ND + 1;                                  // [1] like-particle source count
 
-  const int4 item = g.work[blockIdx.x];
+  const int4 item = g.work[item_index];
   const int pA = item.x, blk = item.y, r0 = item.z, nrows = item.w;
   const int64_t off = h.boff[blk];
   const int nb = h.bnb[blk];
@@ -219,6 +219,24 @@ __global__ void __launch_bounds__(kThreads) apply_grouped_kernel(DevH<T> h, DevG
   }
 }
 
+template <typename T, int LPE, int CPL>
+__global__ void __launch_bounds__(kThreads) apply_grouped_kernel(DevH<T> h, DevG<T> g, const T* __restrict__ V,
+                                                                 int64_t ldv, T* __restrict__ W, int64_t ldw) {
+  grouped_body<T, LPE, CPL>(h, g, blockIdx.x, V, ldv, W, ldw);
+}
+
+// Several Hamiltonians on one basis: blockIdx.y selects the set; set s reads
+// V + s * sv and writes W + s * sw.
+template <typename T, int LPE, int CPL>
+__global__ void __launch_bounds__(kThreads) apply_grouped_batch_kernel(const DevH<T>* __restrict__ hs,
+                                                                       const DevG<T>* __restrict__ gs,
+                                                                       const T* __restrict__ V, int64_t ldv, int64_t sv,
+                                                                       T* __restrict__ W, int64_t ldw, int64_t sw) {
+  const DevH<T> h = hs[blockIdx.y];
+  const DevG<T> g = gs[blockIdx.y];
+  grouped_body<T, LPE, CPL>(h, g, blockIdx.x, V + blockIdx.y * sv, ldv, W + blockIdx.y * sw, ldw);
+}
+
 size_t smem_bytes(int maxP, int maxQ, int maxK, int ND, size_t tsize) {
   return size_t(maxP + 1) * 8 + size_t(maxQ) * 8 + (size_t(maxP + 1) * maxK + maxQ) * tsize +
          size_t(maxP + 1) * 4 + size_t(ND + 2) * 4;
@@ -259,7 +277,51 @@ int launch_typed(const trbl_hamiltonian* hm, const DevH<T>& h, const DevG<T>& g,
   }
 }
 
+template <typename T, int LPE, int CPL>
+int launch_batch_lpe(const DevH<T>* hs, const DevG<T>* gs, int nset, int nwork, size_t sm, const T* V, int64_t ldv,
+                     int64_t sv, T* W, int64_t ldw, int64_t sw, cudaStream_t s) {
+  static bool configured = false;
+  if (sm > 48 * 1024 && !configured) {
+    TRBL_CUDA(cudaFuncSetAttribute(apply_grouped_batch_kernel<T, LPE, CPL>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+    configured = true;
+  }
+  const dim3 grid{static_cast<unsigned>(nwork), static_cast<unsigned>(nset), 1u};
+  apply_grouped_batch_kernel<T, LPE, CPL><<<grid, kThreads, sm, s>>>(hs, gs, V, ldv, sv, W, ldw, sw); note_launch();
+  TRBL_CUDA(cudaGetLastError());
+  return TRBL_OK;
+}
+
+template <typename T>
+int batch_typed(const DevH<T>* hs, const DevG<T>* gs, int nset, int nwork, size_t sm, const T* V, int64_t ldv,
+                int64_t sv, T* W, int64_t ldw, int64_t sw, int q, cudaStream_t s) {
+  switch (q * int(sizeof(T)) / 16) {
+    case 1: return launch_batch_lpe<T, 1, 1>(hs, gs, nset, nwork, sm, V, ldv, sv, W, ldw, sw, s);
+    case 2: return launch_batch_lpe<T, 2, 1>(hs, gs, nset, nwork, sm, V, ldv, sv, W, ldw, sw, s);
+    case 4: return launch_batch_lpe<T, 4, 1>(hs, gs, nset, nwork, sm, V, ldv, sv, W, ldw, sw, s);
+    case 8: return launch_batch_lpe<T, 4, 2>(hs, gs, nset, nwork, sm, V, ldv, sv, W, ldw, sw, s);
+    case 16: return launch_batch_lpe<T, 4, 4>(hs, gs, nset, nwork, sm, V, ldv, sv, W, ldw, sw, s);
+    case 32: return launch_batch_lpe<T, 4, 8>(hs, gs, nset, nwork, sm, V, ldv, sv, W, ldw, sw, s);
+    default: return fail(TRBL_ERR_ARG, "batched product: q * element size must be 16 * 2^i bytes (<= 512)");
+  }
+}
+
 }  // namespace
+
+size_t grouped_smem_bytes(const trbl_hamiltonian* h, int dtype) {
+  const auto& g = h->g32;
+  return smem_bytes(g.maxP, g.maxQ, g.maxK, h->b->ND, dtype == TRBL_F64 ? 8 : 4);
+}
+
+int launch_grouped_batch(const void* hs_dev, const void* gs_dev, int nset, int nwork, size_t smem, const void* V,
+                         int64_t ldv, int64_t sv, void* W, int64_t ldw, int64_t sw, int q, int dtype, cudaStream_t s) {
+  if (dtype == TRBL_F64)
+    return batch_typed<double>(static_cast<const DevH<double>*>(hs_dev), static_cast<const DevG<double>*>(gs_dev),
+                               nset, nwork, smem, static_cast<const double*>(V), ldv, sv, static_cast<double*>(W),
+                               ldw, sw, q, s);
+  return batch_typed<float>(static_cast<const DevH<float>*>(hs_dev), static_cast<const DevG<float>*>(gs_dev), nset,
+                            nwork, smem, static_cast<const float*>(V), ldv, sv, static_cast<float*>(W), ldw, sw, q, s);
+}
 
 int launch_grouped(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, int64_t ldw, int q, int dtype,
                    cudaStream_t s) {
@@ -309,12 +371,6 @@ int upload_grouped(trbl_hamiltonian* h) {
     const int dn = B.twom[B.ja[e]] - B.twom[B.jc[e]] + span;
     jB2[e] = make_int2(loc, (k << 9) | (dn << 1) | (B.jsign[e] < 0 ? 1 : 0));
   }
-  // work items, heaviest first
-  struct Item {
-    int pA, blk, r0, n;
-    long long cost;
-  };
-  std::vector<Item> items;
   int maxP = 1, maxQ = 1;
   const int nblk = int(b->blocks.size());
   for (int k = 0; k < nblk; ++k) {
@@ -328,23 +384,15 @@ int upload_grouped(trbl_hamiltonian* h) {
       const int Q = h->hoff[0][pA + 1] - h->hoff[0][pA];
       maxP = std::max(maxP, P);
       maxQ = std::max(maxQ, Q);
-      for (int r0 = 0; r0 < bl.nb; r0 += kRowsPerItem) {
-        const int n = std::min(kRowsPerItem, bl.nb - r0);
-        items.push_back({pA, k, r0, n, (long long)n * (P * 8 + Q + 64)});
-      }
     }
   }
-  std::vector<int4> work(items.size());
-  for (size_t i = 0; i < items.size(); ++i) work[i] = make_int4(items[i].pA, items[i].blk, items[i].r0, items[i].n);
-  if (items.size() > size_t(0x7fffffff)) return fail(TRBL_ERR_ARG, "too many work items");
   const size_t sm64 = smem_bytes(maxP, maxQ, maxK, ND, 8);
   if (sm64 > 200 * 1024) {
     // tables too large for the grouped kernel: leave it disabled (row kernel serves)
     return TRBL_OK;
   }
 
-  size_t o_work = 0;
-  size_t o_jB2 = (o_work + work.size() * sizeof(int4) + 255) & ~size_t(255);
+  size_t o_jB2 = 0;
   size_t o_c64 = (o_jB2 + jB2.size() * sizeof(int2) + 255) & ~size_t(255);
   size_t o_c32 = (o_c64 + cc.size() * 8 + 255) & ~size_t(255);
   size_t total = o_c32 + cc32.size() * 4 + 256;
@@ -352,14 +400,11 @@ int upload_grouped(trbl_hamiltonian* h) {
   TRBL_CUDA(cudaMalloc(&arena, total));
   h->garena = arena;
   char* base = static_cast<char*>(arena);
-  TRBL_CUDA(cudaMemcpy(base + o_work, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice));
   TRBL_CUDA(cudaMemcpy(base + o_jB2, jB2.data(), jB2.size() * sizeof(int2), cudaMemcpyHostToDevice));
   TRBL_CUDA(cudaMemcpy(base + o_c64, cc.data(), cc.size() * 8, cudaMemcpyHostToDevice));
   TRBL_CUDA(cudaMemcpy(base + o_c32, cc32.data(), cc32.size() * 4, cudaMemcpyHostToDevice));
   auto fill = [&](auto& g, size_t o_c) {
     using TT = typename std::remove_const<typename std::remove_pointer<decltype(g.ccoef)>::type>::type;
-    g.work = reinterpret_cast<const int4*>(base + o_work);
-    g.nwork = int(work.size());
     g.maxP = maxP;
     g.maxQ = maxQ;
     g.maxK = maxK;
@@ -368,6 +413,39 @@ int upload_grouped(trbl_hamiltonian* h) {
   };
   fill(h->g64, o_c64);
   fill(h->g32, o_c32);
+  return set_work_items(h, kRowsPerItem);
+}
+
+// Work items (target proton determinant, block, first neutron row, rows) in
+// basis order, rows_per_item neutron rows each; replaces the current list.
+int set_work_items(trbl_hamiltonian* h, int rows_per_item) {
+  if (rows_per_item < 1) return fail(TRBL_ERR_ARG, "rows per work item must be positive");
+  const trbl_basis* b = h->b;
+  const Species& A = b->sp[0];
+  std::vector<int4> work;
+  for (size_t k = 0; k < b->blocks.size(); ++k) {
+    const Block& bl = b->blocks[k];
+    const int a0 = A.gfirst[bl.gA];
+    for (int ia = 0; ia < bl.na; ++ia)
+      for (int r0 = 0; r0 < bl.nb; r0 += rows_per_item)
+        work.push_back(make_int4(a0 + ia, int(k), r0, std::min(rows_per_item, bl.nb - r0)));
+  }
+  if (work.size() > size_t(0x7fffffff)) return fail(TRBL_ERR_ARG, "too many work items");
+  void* p = nullptr;
+  TRBL_CUDA(cudaMalloc(&p, work.size() * sizeof(int4)));
+  cudaError_t e = cudaMemcpy(p, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(p);
+    return cuda_fail(e, "cudaMemcpy(work items)");
+  }
+  if (h->gwork) {
+    cudaDeviceSynchronize();
+    cudaFree(h->gwork);
+  }
+  h->gwork = p;
+  h->rows_per_item = rows_per_item;
+  h->g64.work = h->g32.work = static_cast<const int4*>(p);
+  h->g64.nwork = h->g32.nwork = int(work.size());
   return TRBL_OK;
 }
 

@@ -117,6 +117,8 @@ struct trbl_hamiltonian {
   trbl::DevG<double> g64;
   trbl::DevG<float> g32;
   void* garena = nullptr;
+  void* gwork = nullptr;   // work items of the grouped kernel
+  int rows_per_item = 0;   // neutron rows per work item (autotuned)
   void* grad = nullptr;  // gradient tables, built on the first trbl_grad call
   size_t arena_bytes = 0;
 };
@@ -129,6 +131,14 @@ namespace trbl {
 int upload_tables(trbl_hamiltonian* h);
 // Builds and uploads the grouped-kernel tables (apply_grouped.cu).
 int upload_grouped(trbl_hamiltonian* h);
+// Replaces the grouped kernel's work items (rows_per_item rows each).
+int set_work_items(trbl_hamiltonian* h, int rows_per_item);
+// Dynamic shared memory of the grouped kernel for one Hamiltonian.
+size_t grouped_smem_bytes(const trbl_hamiltonian* h, int dtype);
+// One launch of the grouped kernel over nset Hamiltonians (device arrays of
+// DevH<T> / DevG<T>), set s reading V + s*sv and writing W + s*sw.
+int launch_grouped_batch(const void* hs_dev, const void* gs_dev, int nset, int nwork, size_t smem, const void* V,
+                         int64_t ldv, int64_t sv, void* W, int64_t ldw, int64_t sw, int q, int dtype, cudaStream_t s);
 // Enqueues W = H V with the grouped kernel when q and the alignment allow it;
 // returns -1 (nothing launched) otherwise.
 int launch_grouped(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, int64_t ldw, int q,

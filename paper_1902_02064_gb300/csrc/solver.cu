@@ -29,6 +29,7 @@
 #include <cstdlib>
 #include <type_traits>
 #include <cmath>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -295,6 +296,7 @@ struct Solver {
   int* hflags;
   uint64_t reseed = 0;
   double normH = 0.0;
+  bool skip_warmup = false;  // batch members after the first share the warmed eigensolver
 
   ~Solver() {
     if (t0) cudaEventDestroy(t0);
@@ -321,6 +323,18 @@ struct Solver {
   // Cholesky QR twice: Vk = W R^{-1}, beta = R2 R1.  Returns the number of
   // deficient columns found in pass 1 (their flags stay in hflags).
   int cholqr2(T* Win, double thresh_abs, double thresh_rel, double thresh_max, int* ndef) {
+    TRY(cholqr2_async(Win, thresh_abs, thresh_rel, thresh_max));
+    TRY(tma_error_to_host(hflags + kTmaErr, s));
+    TRY(dot_error_to_host(hflags + kTmaErr + 1, s));
+    TRBL_CUDA(cudaStreamSynchronize(s));
+    if (hflags[kTmaErr] || hflags[kTmaErr + 1]) return fail(TRBL_ERR_CUDA, "a TMA wait in a projection timed out");
+    *ndef = hflags[kF1] + hflags[kF2];
+    return TRBL_OK;
+  }
+
+  // Cholesky QR twice, enqueued only: the deficiency counts are copied to
+  // pinned host memory (hflags) for the caller to read after synchronising.
+  int cholqr2_async(T* Win, double thresh_abs, double thresh_rel, double thresh_max) {
     TRY(block_dot<T>(Win, q, q, Win, q, q, D, G, ws, s));
     chol_kernel<<<1, 64, 0, s>>>(G, q, thresh_abs, thresh_rel, thresh_max, R1, R1i, flags + kF1); note_launch();
     TRBL_CUDA(cudaGetLastError());
@@ -333,11 +347,6 @@ struct Solver {
     TRY(rowgemm<T>(W2, q, q, R2i, q, q, Vk, q, D, 1.0, 0.0, s));
     upper_mul_kernel<<<(q * q + 127) / 128, 128, 0, s>>>(R2, R1, q, beta); note_launch();
     TRBL_CUDA(cudaGetLastError());
-    TRY(tma_error_to_host(hflags + kTmaErr, s));
-    TRY(dot_error_to_host(hflags + kTmaErr + 1, s));
-    TRBL_CUDA(cudaStreamSynchronize(s));
-    if (hflags[kTmaErr] || hflags[kTmaErr + 1]) return fail(TRBL_ERR_CUDA, "a TMA wait in a projection timed out");
-    *ndef = hflags[kF1] + hflags[kF2];
     return TRBL_OK;
   }
 
@@ -523,6 +532,59 @@ struct Solver {
     return TRBL_OK;
   }
 
+  // ---- pieces of a block step for the batched driver ----
+  // Everything after W = H V_k with no host synchronisation: CGS2, alpha,
+  // Cholesky QR twice, and (unless the basis is full) beta and the append of
+  // V_{k+1}.  Safe to capture in a CUDA graph for a fixed nb.
+  int step_device(bool append) {
+    double* C1 = C + size_t(2) * mb * q;
+    TRY(cgs2(W, nb, C1));
+    set_alpha_kernel<<<(q * q + 127) / 128, 128, 0, s>>>(Tm, mb, C1, nb - q, q); note_launch();
+    TRBL_CUDA(cudaGetLastError());
+    TRY(cholqr2_async(W, tau * normH, 0.0, tau_max));
+    if (append) {
+      set_beta_kernel<<<(q * q + 127) / 128, 128, 0, s>>>(Tm, mb, beta, nb, nb - q, q); note_launch();
+      TRBL_CUDA(cudaGetLastError());
+      TRY(copy_cols<T, T>(Vk, q, basis + nb, mb, D, q, s));
+    }
+    return TRBL_OK;
+  }
+
+  // After step_device ran (stream synchronised): deficiency check, Rayleigh-
+  // Ritz when due, and the thick restart when the basis was full.
+  int step_after(bool appended, int check_every, int max_iter) {
+    if (hflags[kF1] + hflags[kF2] > 0)
+      return fail(TRBL_ERR_BREAKDOWN, "batched step: rank-deficient block (the batched driver has no repair path)");
+    ++iter;
+    const int nb_old = nb;
+    const bool check = !appended || iter % check_every == 0 || iter >= max_iter;
+    if (check && !done) {
+      TRY(ritz(nb_old));
+      const double lim = p->tol * normH;
+      conv = 0;
+      for (int i = 0; i < std::min(nev, nb_old); ++i)
+        if (hbuf[mb + i] <= lim) ++conv;
+      if (nb_old >= nev && conv == nev) done = true;
+    }
+    if (appended) {
+      nb += q;
+      have_ritz = false;
+    } else {
+      // all sets of a batch share one basis schedule, so a set that has
+      // converged restarts with the others (its kept Ritz pairs survive)
+      if (!check || done) TRY(ritz(nb_old));
+      TRY(compress(nb_old, ls));
+      TRBL_CUDA(cudaMemsetAsync(Tm, 0, sizeof(double) * mb * mb, s));
+      restart_t_kernel<<<(ls * q + 127) / 128, 128, 0, s>>>(Tm, mb, theta, beta, q, Aw, mb, nb_old, ls); note_launch();
+      TRBL_CUDA(cudaGetLastError());
+      TRY(copy_cols<T, T>(Vk, q, basis + ls, mb, D, q, s));
+      nb = ls + q;
+      have_ritz = false;
+      ++restarts;
+    }
+    return TRBL_OK;
+  }
+
   void fill_stats(trbl_stats* st, int status) {
     st->iterations = iter;
     st->restarts = restarts;
@@ -676,7 +738,7 @@ struct Solver {
     // The eigensolver loads size-dependent kernel variants on first use,
     // which can take seconds; run it once per size class here so that the
     // iteration does not pay it.
-    for (int n = q; n <= mb; n = (n < mb && 2 * n > mb) ? mb : 2 * n) {
+    for (int n = q; !skip_warmup && n <= mb; n = (n < mb && 2 * n > mb) ? mb : 2 * n) {
       TRBL_CUDA(cudaMemsetAsync(Aw, 0, sizeof(double) * size_t(mb) * n, s));
       TRBL_SOLVER(cusolverDnDsyevd(sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, Aw, mb, theta,
                                    syev_work, lwork, devinfo));
@@ -719,6 +781,190 @@ struct SolverImpl : SolverBase {
   size_t block_bytes() override { return sizeof(T) * size_t(S.D) * S.q; }
   bool is_done() override { return S.done; }
   int iterations() override { return S.iter; }
+};
+
+}  // namespace
+}  // namespace trbl
+
+namespace trbl {
+namespace {
+
+// Several Hamiltonians on one basis solved together: one persistent launch
+// applies all of them (the grouped kernel over work items x sets), the rest
+// of a block step for every set is captured once per basis size into a CUDA
+// graph and replayed; Rayleigh-Ritz tests and restarts run between replays.
+template <typename T>
+struct BatchDriver {
+  std::vector<Solver<T>*> sets;
+  trbl_params prm{};
+  cudaStream_t s = nullptr;
+  int nset = 0, nwork = 0, dtype = 0;
+  size_t smem = 0;
+  int64_t D = 0;
+  int q = 0, mb = 0;
+  void* shared = nullptr;  // V_k and W of all sets, set-major
+  void* tables = nullptr;  // DevH<T>[nset], DevG<T>[nset]
+  std::map<int, cudaGraphExec_t> graphs;
+  int graph_replays = 0;
+
+  ~BatchDriver() {
+    if (s) cudaStreamSynchronize(s);
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    for (auto* S : sets) delete S;
+    if (shared) cudaFree(shared);
+    if (tables) cudaFree(tables);
+  }
+
+  int setup(const trbl_hamiltonian* const* hs) {
+    const trbl_basis* b = hs[0]->b;
+    D = b->D;
+    q = prm.q;
+    mb = prm.max_basis;
+    dtype = std::is_same<T, double>::value ? TRBL_F64 : TRBL_F32;
+    const int bytes = q * int(sizeof(T));
+    if (bytes % 16 || (bytes & (bytes - 1)) || bytes > 512)
+      return fail(TRBL_ERR_ARG, "batched solve needs q * element size = 16 * 2^i bytes (<= 512)");
+    for (int i = 0; i < nset; ++i) {
+      if (!hs[i] || hs[i]->b != b) return fail(TRBL_ERR_ARG, "batched Hamiltonians must share one basis");
+      if (!hs[i]->garena) return fail(TRBL_ERR_ARG, "the grouped product is not available for this basis");
+      if (hs[i]->rows_per_item != hs[0]->rows_per_item)
+        TRY(set_work_items(const_cast<trbl_hamiltonian*>(hs[i]), hs[0]->rows_per_item));
+      smem = std::max(smem, grouped_smem_bytes(hs[i], dtype));
+    }
+    nwork = hs[0]->g32.nwork;
+    const size_t dq = size_t(D) * q;
+    TRBL_CUDA(cudaMalloc(&shared, sizeof(T) * dq * 2 * nset));
+    TRBL_CUDA(cudaMalloc(&tables, (sizeof(DevH<T>) + sizeof(DevG<T>)) * nset));
+    std::vector<DevH<T>> hv(nset);
+    std::vector<DevG<T>> gv(nset);
+    for (int i = 0; i < nset; ++i) {
+      if constexpr (std::is_same<T, double>::value) {
+        hv[i] = hs[i]->d64;
+        gv[i] = hs[i]->g64;
+      } else {
+        hv[i] = hs[i]->d32;
+        gv[i] = hs[i]->g32;
+      }
+    }
+    TRBL_CUDA(cudaMemcpy(tables, hv.data(), sizeof(DevH<T>) * nset, cudaMemcpyHostToDevice));
+    TRBL_CUDA(cudaMemcpy(static_cast<char*>(tables) + sizeof(DevH<T>) * nset, gv.data(), sizeof(DevG<T>) * nset,
+                         cudaMemcpyHostToDevice));
+    T* V0 = static_cast<T*>(shared);
+    T* W0 = V0 + dq * nset;
+    for (int i = 0; i < nset; ++i) {
+      auto* S = new (std::nothrow) Solver<T>{};
+      if (!S) return fail(TRBL_ERR_OOM, "host allocation failed");
+      sets.push_back(S);
+      S->h = hs[i];
+      S->p = &prm;
+      S->s = s;
+      S->skip_warmup = i > 0;
+      TRY(S->setup());
+      S->Vk = V0 + dq * i;
+      S->W = W0 + dq * i;
+      TRY(S->init());
+    }
+    return TRBL_OK;
+  }
+
+  // batched product for all sets, then each set's device step
+  int enqueue(bool append) {
+    T* V0 = static_cast<T*>(shared);
+    const size_t dq = size_t(D) * q;
+    TRY(launch_grouped_batch(tables, static_cast<char*>(tables) + sizeof(DevH<T>) * nset, nset, nwork, smem, V0, q,
+                             int64_t(dq), V0 + dq * nset, q, int64_t(dq), q, dtype, s));
+    for (auto* S : sets) TRY(S->step_device(append));
+    return TRBL_OK;
+  }
+
+  int graph_for(int nb, bool append, cudaGraphExec_t* out) {
+    auto it = graphs.find(nb);
+    if (it != graphs.end()) {
+      *out = it->second;
+      return TRBL_OK;
+    }
+    cudaGraph_t g = nullptr;
+    TRBL_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue(append);
+    const cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    TRBL_CUDA(e);
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    TRBL_CUDA(ei);
+    graphs[nb] = ex;
+    *out = ex;
+    return TRBL_OK;
+  }
+
+  int run(double* evals, double* resid, void* evecs, int* status, trbl_stats* st) {
+    const int nev = prm.nev;
+    const int check_every = prm.check_every > 0 ? prm.check_every : std::max(1, 32 / q);
+    const int max_iter = prm.max_iter > 0 ? prm.max_iter : 100000;
+    std::vector<int> rc(nset, TRBL_OK);
+    cudaEvent_t t0, t1;
+    TRBL_CUDA(cudaEventCreate(&t0));
+    TRBL_CUDA(cudaEventCreate(&t1));
+    TRBL_CUDA(cudaEventRecord(t0, s));
+    int it = 0;
+    for (; it < max_iter; ++it) {
+      bool all = true;
+      for (int i = 0; i < nset; ++i) all = all && (sets[i]->done || rc[i] != TRBL_OK);
+      if (all) break;
+      const int nb = sets[0]->nb;
+      const bool append = nb + q <= mb;
+      if (it == 0) {
+        TRY(enqueue(append));  // eager first step: lazily configured kernels set up outside capture
+      } else {
+        cudaGraphExec_t ex;
+        TRY(graph_for(nb, append, &ex));
+        TRBL_CUDA(cudaGraphLaunch(ex, s));
+        ++graph_replays;
+      }
+      TRBL_CUDA(cudaStreamSynchronize(s));
+      for (int i = 0; i < nset; ++i) {
+        if (rc[i] != TRBL_OK) continue;
+        rc[i] = sets[i]->step_after(append, check_every, max_iter);
+      }
+    }
+    for (int i = 0; i < nset; ++i) {
+      Solver<T>* S = sets[i];
+      if (rc[i] == TRBL_OK) {
+        const int r = S->finish(evals + size_t(i) * nev, resid ? resid + size_t(i) * nev : nullptr,
+                                evecs ? static_cast<T*>(evecs) + size_t(i) * D * nev : nullptr, nullptr);
+        rc[i] = r;
+      } else {
+        for (int k = 0; k < nev; ++k) evals[size_t(i) * nev + k] = NAN;
+      }
+      if (status) status[i] = rc[i];
+    }
+    TRBL_CUDA(cudaEventRecord(t1, s));
+    TRBL_CUDA(cudaStreamSynchronize(s));
+    int worst = TRBL_OK, conv = 0;
+    for (int i = 0; i < nset; ++i) {
+      if (rc[i] != TRBL_OK && worst == TRBL_OK) worst = rc[i];
+      conv += sets[i]->conv;
+    }
+    if (st) {
+      *st = trbl_stats{};
+      float tot = 0.f;
+      cudaEventElapsedTime(&tot, t0, t1);
+      st->iterations = it;
+      st->restarts = sets[0]->restarts;
+      st->converged = conv;
+      st->status = worst;
+      st->normH = sets[0]->normH;
+      st->ms_total = tot;
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (worst != TRBL_OK) return fail(worst, "batched solve: %d of %d sets did not finish cleanly", int(std::count_if(rc.begin(), rc.end(), [](int x) { return x != TRBL_OK; })), nset);
+    return TRBL_OK;
+  }
 };
 
 }  // namespace
@@ -841,5 +1087,42 @@ extern "C" int trbl_solve(const trbl_hamiltonian* h, const trbl_params* p, doubl
   trbl_solver_destroy(sv);
   if (rc != TRBL_OK) fail(rc, "%s", keep.c_str());
   if (stats) stats->status = rc;
+  return rc;
+}
+
+extern "C" int trbl_solve_batch(const trbl_hamiltonian* const* hs, int nset, const trbl_params* p, double* evals,
+                                double* resid, void* evecs, int* status, trbl_stats* stats, void* stream) {
+  clear_error();
+  if (!hs || nset < 1 || !p || !evals) return fail(TRBL_ERR_ARG, "null argument or empty batch");
+  // CUDA graphs cannot be captured on the legacy default stream: run on a
+  // private stream ordered after the caller's.
+  cudaStream_t caller = static_cast<cudaStream_t>(stream);
+  cudaStream_t s = nullptr;
+  cudaEvent_t ready = nullptr;
+  TRBL_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  TRBL_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  TRBL_CUDA(cudaEventRecord(ready, caller));
+  TRBL_CUDA(cudaStreamWaitEvent(s, ready, 0));
+  int rc;
+  if (p->precision == TRBL_PREC_F64) {
+    BatchDriver<double> B;
+    B.prm = *p;
+    B.s = s;
+    B.nset = nset;
+    rc = B.setup(hs);
+    if (!rc) rc = B.run(evals, resid, evecs, status, stats);
+  } else if (p->precision == TRBL_PREC_MIXED) {
+    BatchDriver<float> B;
+    B.prm = *p;
+    B.s = s;
+    B.nset = nset;
+    rc = B.setup(hs);
+    if (!rc) rc = B.run(evals, resid, evecs, status, stats);
+  } else {
+    rc = fail(TRBL_ERR_ARG, "precision must be TRBL_PREC_F64 or TRBL_PREC_MIXED");
+  }
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(ready);
+  cudaStreamDestroy(s);
   return rc;
 }
