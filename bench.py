@@ -20,6 +20,7 @@ Multi-GPU (torchrun): every rank solves its own independent replica
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -173,12 +174,21 @@ def measured_peaks():
 
 
 def ncu_traffic(path=os.path.join(ROOT, "profiles", "apply_traffic.json")):
-    """DRAM bytes per apply launch from a committed ncu summary, if current."""
+    """(DRAM bytes per apply launch, kernel name) from a committed ncu summary.
+    The bytes are None unless the summary was taken on the kernel source as it
+    is now (its SHA-256 is stored beside the figure)."""
     try:
         d = json.load(open(path))
-        return d.get("dram_bytes_per_launch_full_size")
     except (OSError, ValueError):
-        return None
+        return None, None
+    src = os.path.join(ROOT, "paper_1902_02064_gb300", "csrc", "apply_grouped.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        sha = None
+    if d.get("source_sha256") != sha:
+        return None, d.get("kernel")
+    return d.get("dram_bytes_per_launch_full_size"), d.get("kernel")
 
 
 # ----------------------------------------------------------------------------
@@ -327,6 +337,7 @@ def run_ours(args, rank, world):
     value = world * nnz * q * args.steps / (ms * 1e-3) / 1e9
     ms_apply = (st1["ms_apply"] - st0["ms_apply"]) / args.steps
     achieved = b_slab / (ms_apply * 1e-3) / 1e9
+    traffic, _ = ncu_traffic()
 
     # end to end: the same steps with V_k supplied from and V_{k+1} returned to
     # pinned host memory through the C ABI (trbl_solver_step_host)
@@ -365,8 +376,8 @@ def run_ours(args, rank, world):
         "phases_ms_per_step": {k: (st1[k] - st0[k]) / args.steps
                                for k in ("ms_apply", "ms_orth", "ms_qr", "ms_ritz", "ms_restart")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": ncu_traffic(),
-                     "kernel": "apply_rows_kernel<float>",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "apply_grouped_kernel<float, 4, 2>",
                      "algorithmic_bytes_per_launch": b_slab,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"},
         "clocks": clk,
@@ -376,6 +387,8 @@ def run_ours(args, rank, world):
     }
     if rank == 0 and world == 1 and not args.no_ttn:
         line["time_to_nev"] = time_to_nev(trbl)
+    if rank == 0 and world == 1 and not args.no_batch:
+        line["gradient_batch"] = gradient_batch(trbl)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, q, args.cpu_seconds)
     del sv
@@ -412,6 +425,48 @@ def time_to_nev(trbl, name="s12_4p4n"):
                       "max_true_resid_over_normH": float(np.nanmax(rs) / normH),
                       "phase_ms": {k: st[k] for k in ("ms_apply", "ms_orth", "ms_qr", "ms_ritz", "ms_restart")}}
     return out
+
+
+def gradient_batch(trbl, nset=64):
+    """Gradient batch: nset parameter sets (seeds 100..) of the 12-m-state 4+4
+    space (D = 28,503), the 20 lowest eigenpairs each (q = 8, basis 256, FP64)
+    and the Hellmann-Feynman gradient of every level cluster, solved as one
+    batch (trbl_solve_batch) and as nset single solves."""
+    import torch
+    sp = synth.make_space(synth.SPACE12_SHELLS)
+    tb = trbl.Basis(sp, 4, sp, 4, 0)
+    inters = [synth.draw_interaction(sp, sp, 100 + k) for k in range(nset)]
+    hs = [trbl.Hamiltonian.from_interaction(tb, it) for it in inters]
+    nev, q, mb, tol = 20, 8, 256, 1e-10
+    ms, rows = trbl.apply_autotune(hs[0], q, trbl.TRBL_F64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev, rs, X, status, st = trbl.solve_batch(hs, nev, q, mb, tol, want_vectors=True, want_resid=False)
+    torch.cuda.synchronize()
+    t_solve_b = time.perf_counter() - t0
+    euler = 0.0
+    for k in range(nset):
+        for cl in trbl.clusters_of(ev[k], 1e-8 * st["normH"]):
+            g = trbl.hf_gradient(hs[k], X[k], cl)
+            euler = max(euler, abs(g @ inters[k].theta - ev[k][cl].sum()) / st["normH"])
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    max_diff = 0.0
+    for k in range(nset):
+        e1, r1, X1, st1 = trbl.solve(hs[k], nev, q, mb, tol)
+        for cl in trbl.clusters_of(e1, 1e-8 * st1["normH"]):
+            trbl.hf_gradient(hs[k], X1, cl)
+        max_diff = max(max_diff, float(np.abs(e1 - ev[k]).max()))
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    return {"sets": nset, "dim": tb.dim, "nev": nev, "q": q, "params_per_set": len(inters[0].theta),
+            "autotune_ms": ms, "rows_per_item": rows,
+            "batched_solve_s": t_solve_b, "batched_solve_plus_gradients_s": t_batch,
+            "sequential_solves_plus_gradients_s": t_seq, "speedup": t_seq / t_batch,
+            "sets_ok": int(sum(1 for x in status if x == 0)), "graph_steps": st["iterations"],
+            "max_eig_diff_batch_vs_single_over_normH": max_diff / st["normH"],
+            "max_euler_identity_error_over_normH": euler}
 
 
 def run_apply_only(args):
@@ -460,6 +515,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttn", action="store_true", help="skip the time-to-nev solves")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-set gradient batch")
     ap.add_argument("--apply-only", default=None, help="time only W = H V on this workload")
     ap.add_argument("--workload", default=WORKLOAD, help="workload of the solver steps (default: the 5+5 space)")
     ap.add_argument("--q", type=int, default=0)

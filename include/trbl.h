@@ -209,7 +209,8 @@ typedef struct trbl_params {
   int precision;       /* TRBL_PREC_F64 or TRBL_PREC_MIXED */
   int max_iter;        /* block iterations cap; 0 = 100000 */
   int check_every;     /* Rayleigh-Ritz convergence test every this many block steps (restarts always
-                          test); 0 = one test per 32 new Lanczos vectors, max(1, 32 / q) steps */
+                          test); 0 = adaptive: a test once the block steps since the previous test
+                          have taken at least as long as that test did */
   uint64_t seed;       /* start block: uniform(-1,1) from splitmix64(seed<<32 + i*q + j) */
   double normH;        /* ||H|| used by tol; 0 = estimated by the solver (largest |Ritz value|) */
 } trbl_params;
@@ -242,9 +243,14 @@ int trbl_solve(const trbl_hamiltonian* h, const trbl_params* p, double* evals, d
 /* Batched form of trbl_solve for nset Hamiltonians built on one basis (for
  * example many parameter sets of one model space), all with the same
  * parameters p.  One persistent launch of the block product serves every
- * set; the rest of a block step for all sets is captured into a CUDA graph
- * per basis size and replayed; Rayleigh-Ritz tests and restarts run between
- * replays.  Outputs are set-major: evals and resid [nset * nev] (host),
+ * set; the rest of a block step runs on one stream per set, forked from and
+ * joined back into a private stream, and that step is captured into a CUDA
+ * graph per basis size and replayed.  Rayleigh-Ritz tests and restarts run
+ * between replays on host worker threads (each set on its own stream), all
+ * sets testing at the same steps.  stats: iterations = block steps, ms_total
+ * = wall time of the whole call, ms_apply = wall time of the batched block
+ * steps (product, orthogonalisation, QR of every set), ms_ritz = wall time
+ * of the tests and restarts between them.  Outputs are set-major: evals and resid [nset * nev] (host),
  * evecs [nset][D x nev] (device, may be NULL), status [nset] (host, per-set
  * return code, may be NULL); stats summarises the batch.  Needs
  * q * element size = 16 * 2^i bytes.  A rank-deficient block stops its set

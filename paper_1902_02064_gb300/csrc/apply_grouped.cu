@@ -36,6 +36,7 @@ namespace {
 
 constexpr int kRowsPerItem = 128;
 constexpr int kThreads = 256;
+constexpr int kMaxSmem = 227 * 1024;  // dynamic shared memory limit of a block on sm_103a
 
 template <typename T>
 struct Vec16;
@@ -245,12 +246,11 @@ size_t smem_bytes(int maxP, int maxQ, int maxK, int ND, size_t tsize) {
 template <typename T, int LPE, int CPL>
 int launch_lpe(const DevH<T>& h, const DevG<T>& g, const T* V, int64_t ldv, T* W, int64_t ldw, cudaStream_t s) {
   const size_t sm = smem_bytes(g.maxP, g.maxQ, g.maxK, h.ND, sizeof(T));
-  static bool configured = false;
-  if (sm > 48 * 1024 && !configured) {
-    TRBL_CUDA(cudaFuncSetAttribute(apply_grouped_kernel<T, LPE, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   int(sm)));
-    configured = true;
-  }
+  // opt in once to the largest dynamic shared memory a block may use (thread-safe initialisation)
+  static const cudaError_t cfg = cudaFuncSetAttribute(apply_grouped_kernel<T, LPE, CPL>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+  TRBL_CUDA(cfg);
+  if (sm > size_t(kMaxSmem)) return fail(TRBL_ERR_ARG, "product needs %zu bytes of shared memory", sm);
   apply_grouped_kernel<T, LPE, CPL><<<g.nwork, kThreads, sm, s>>>(h, g, V, ldv, W, ldw); note_launch();
   TRBL_CUDA(cudaGetLastError());
   return TRBL_OK;
@@ -280,12 +280,10 @@ int launch_typed(const trbl_hamiltonian* hm, const DevH<T>& h, const DevG<T>& g,
 template <typename T, int LPE, int CPL>
 int launch_batch_lpe(const DevH<T>* hs, const DevG<T>* gs, int nset, int nwork, size_t sm, const T* V, int64_t ldv,
                      int64_t sv, T* W, int64_t ldw, int64_t sw, cudaStream_t s) {
-  static bool configured = false;
-  if (sm > 48 * 1024 && !configured) {
-    TRBL_CUDA(cudaFuncSetAttribute(apply_grouped_batch_kernel<T, LPE, CPL>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-    configured = true;
-  }
+  static const cudaError_t cfg = cudaFuncSetAttribute(apply_grouped_batch_kernel<T, LPE, CPL>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+  TRBL_CUDA(cfg);
+  if (sm > size_t(kMaxSmem)) return fail(TRBL_ERR_ARG, "product needs %zu bytes of shared memory", sm);
   const dim3 grid{static_cast<unsigned>(nwork), static_cast<unsigned>(nset), 1u};
   apply_grouped_batch_kernel<T, LPE, CPL><<<grid, kThreads, sm, s>>>(hs, gs, V, ldv, sv, W, ldw, sw); note_launch();
   TRBL_CUDA(cudaGetLastError());

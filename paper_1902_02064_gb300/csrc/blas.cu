@@ -384,12 +384,9 @@ int block_dot(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, in
 template <typename T, int NP>
 int tall_launch(const T* In, int64_t ldi, int K, const double* U, int64_t ldu, int n, T* Out, int64_t ldo,
                 int64_t D, double alpha, double beta, cudaStream_t s, size_t smem, int sms) {
-  static bool configured = false;
-  if (!configured) {
-    TRBL_CUDA(cudaFuncSetAttribute(rowgemm_tall_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   228 * 1024 - 1024));
-    configured = true;
-  }
+  static const cudaError_t cfg = cudaFuncSetAttribute(rowgemm_tall_kernel<T, NP>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  TRBL_CUDA(cfg);
   constexpr int RT = 4 * (512 / (NP / 4));
   const int64_t ntiles = (D + RT - 1) / RT;
   const int grid = int(std::min<int64_t>(ntiles, sms));
@@ -418,13 +415,12 @@ int rowgemm(const T* In, int64_t ldi, int K, const double* U, int64_t ldu, int n
     const int Kp = (K + 31) / 32 * 32;
     const size_t smem = (size_t(Kp) * NP + size_t(2) * 32 * (RT + 4)) * sizeof(T);
     if (smem <= 200 * 1024) {
-      static int sms = 0;
-      if (!sms) {
-        int dev = 0;
+      static const int sms = [] {
+        int dev = 0, n = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 148;
-      }
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return n > 0 ? n : 148;
+      }();
       if (NP == 16) return tall_launch<T, 16>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta, s, smem, sms);
       if (NP == 32) return tall_launch<T, 32>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta, s, smem, sms);
       return tall_launch<T, 64>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta, s, smem, sms);

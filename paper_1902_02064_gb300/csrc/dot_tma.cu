@@ -142,11 +142,9 @@ int block_dot_tma(const float* B, int64_t ldb, int m, const float* W, int64_t ld
   if (!rc) rc = make_tmap_2d_f32(&tw, W, uint64_t(q), uint64_t(D), uint64_t(ldw), 32, kRS);
   if (rc) return rc;
   const size_t smem = size_t(kStages) * 5 * kBox * 4 + 8 * kStages + 16;
-  static bool configured = false;
-  if (!configured) {
-    TRBL_CUDA(cudaFuncSetAttribute(block_dot_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    configured = true;
-  }
+  static const cudaError_t cfg =
+      cudaFuncSetAttribute(block_dot_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  TRBL_CUDA(cfg);
   const int nbox = std::min(4, (m + 31) / 32);
   dim3 grid(mtiles, unsigned(nchunk));
   block_dot_tma_kernel<<<grid, 256, smem, s>>>(tb, tw, m, q, D, rows, nbox, partial); note_launch();

@@ -130,13 +130,12 @@ __global__ void __launch_bounds__(NP * 16) rowgemm_tma_kernel(const __grid_const
 template <int NP>
 int launch_np(const CUtensorMap& map, int K, const double* U, int64_t ldu, int n, float* Out, int64_t ldo, int64_t D,
               double alpha, double beta, cudaStream_t s) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
+  static const int sms = [] {
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 148;
-  }
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 148;
+  }();
   const int Kp = (K + kKC - 1) / kKC * kKC;
   const size_t ubytes = size_t(Kp) * NP * 4;
   const size_t stage = size_t(kRT) * kKC * 4;
@@ -145,11 +144,9 @@ int launch_np(const CUtensorMap& map, int K, const double* U, int64_t ldu, int n
   while (nstage > 2 && size_t(nstage) * stage + ubytes + 64 > limit) --nstage;
   const size_t smem = size_t(nstage) * stage + ubytes + 8 * size_t(nstage) + 16;
   if (smem > limit) return -1;
-  static bool configured = false;
-  if (!configured) {
-    TRBL_CUDA(cudaFuncSetAttribute(rowgemm_tma_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(limit)));
-    configured = true;
-  }
+  static const cudaError_t cfg =
+      cudaFuncSetAttribute(rowgemm_tma_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(limit));
+  TRBL_CUDA(cfg);
   const int64_t ntiles = (D + kRT - 1) / kRT;
   const int per_sm = smem * 2 <= limit ? 2 : 1;
   const int grid = int(std::min<int64_t>(ntiles, int64_t(sms) * per_sm));
@@ -166,14 +163,15 @@ int make_tmap_2d_f32(CUtensorMap* map, const void* base, uint64_t cols, uint64_t
   using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-  static EncodeFn encode = nullptr;
-  if (!encode) {
+  static const EncodeFn encode = []() -> EncodeFn {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
-    TRBL_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
-    if (q != cudaDriverEntryPointSuccess || !fn) return fail(TRBL_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-    encode = reinterpret_cast<EncodeFn>(fn);
-  }
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<EncodeFn>(fn);
+  }();
+  if (!encode) return fail(TRBL_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   const cuuint64_t dims[2] = {cols, rows};
   const cuuint64_t strides[1] = {ld * 4};
   const cuuint32_t box[2] = {box_cols, box_rows};

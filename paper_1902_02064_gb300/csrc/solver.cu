@@ -30,8 +30,10 @@
 #include <type_traits>
 #include <cmath>
 #include <map>
+#include <atomic>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "blas.cuh"
@@ -218,12 +220,11 @@ constexpr int kFlagInts = 192;
 
 // Host-side progress trace, on when the environment sets TRBL_TRACE=1.
 static bool trace_on() {
-  static int on = -1;
-  if (on < 0) {
+  static const bool on = [] {
     const char* e = getenv("TRBL_TRACE");
-    on = (e && e[0] == '1') ? 1 : 0;
-  }
-  return on == 1;
+    return e && e[0] == '1';
+  }();
+  return on;
 }
 static void trace(const char* fmt, ...) {
   if (!trace_on()) return;
@@ -445,6 +446,7 @@ struct Solver {
   Timer tm;
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   double ms_apply = 0, ms_orth = 0, ms_qr = 0, ms_ritz = 0, ms_restart = 0;
+  double since_check_ms = 0, last_check_ms = 0;  // adaptive Rayleigh-Ritz cadence
   int nb = 0, iter = 0, restarts = 0, conv = 0;
   bool done = false, have_ritz = false, finished = false;
 
@@ -471,8 +473,6 @@ struct Solver {
       if (conv_out) *conv_out = conv;
       return TRBL_OK;
     }
-    // default cadence: one Rayleigh-Ritz test per 32 new Lanczos vectors
-    const int check_every = p->check_every > 0 ? p->check_every : std::max(1, 32 / q);
     const int max_iter = p->max_iter > 0 ? p->max_iter : 100000;
     trace("iter %d nb %d", iter, nb);
     tm.rec(0, s);
@@ -487,7 +487,10 @@ struct Solver {
     tm.rec(3, s);
     ++iter;
     const bool need_restart = nb + q > mb;
-    const bool check = need_restart || iter % check_every == 0 || iter >= max_iter;
+    // Rayleigh-Ritz cadence: every check_every steps, or (check_every = 0)
+    // once the block steps since the previous test took as long as that test
+    const bool due = p->check_every > 0 ? iter % p->check_every == 0 : since_check_ms >= last_check_ms;
+    const bool check = need_restart || due || iter >= max_iter;
     have_ritz = false;
     if (check) {
       TRY(ritz(nb));
@@ -527,6 +530,12 @@ struct Solver {
     ms_qr += tm.ms(2, 3);
     ms_ritz += tm.ms(3, 4);
     ms_restart += tm.ms(4, 5);
+    if (check) {
+      last_check_ms = tm.ms(3, 4);
+      since_check_ms = 0;
+    } else {
+      since_check_ms += tm.ms(0, 3) + tm.ms(4, 5);
+    }
     trace("step %d phases ms: apply %.2f orth %.2f qr %.2f ritz %.2f restart %.2f", iter, tm.ms(0, 1), tm.ms(1, 2),
           tm.ms(2, 3), tm.ms(3, 4), tm.ms(4, 5));
     return TRBL_OK;
@@ -552,12 +561,12 @@ struct Solver {
 
   // After step_device ran (stream synchronised): deficiency check, Rayleigh-
   // Ritz when due, and the thick restart when the basis was full.
-  int step_after(bool appended, int check_every, int max_iter) {
+  int step_after(bool appended, bool check_due, int max_iter) {
     if (hflags[kF1] + hflags[kF2] > 0)
       return fail(TRBL_ERR_BREAKDOWN, "batched step: rank-deficient block (the batched driver has no repair path)");
     ++iter;
     const int nb_old = nb;
-    const bool check = !appended || iter % check_every == 0 || iter >= max_iter;
+    const bool check = !appended || check_due || iter >= max_iter;
     if (check && !done) {
       TRY(ritz(nb_old));
       const double lim = p->tol * normH;
@@ -789,33 +798,104 @@ struct SolverImpl : SolverBase {
 namespace trbl {
 namespace {
 
-// Several Hamiltonians on one basis solved together: one persistent launch
-// applies all of them (the grouped kernel over work items x sets), the rest
-// of a block step for every set is captured once per basis size into a CUDA
-// graph and replayed; Rayleigh-Ritz tests and restarts run between replays.
+// Several Hamiltonians on one basis solved together.  One persistent launch
+// applies all of them (the grouped kernel over work items x sets); the rest
+// of a block step of every set runs on that set's own stream, forked from
+// and joined back into the driver's stream, and the whole step is captured
+// once per basis size into a CUDA graph and replayed.  Rayleigh-Ritz tests
+// and restarts run between replays on host worker threads, each set on its
+// own stream, so the small eigensolver calls of different sets overlap on
+// the GPU instead of running one after another.
 template <typename T>
 struct BatchDriver {
+  using clock = std::chrono::steady_clock;
   std::vector<Solver<T>*> sets;
   trbl_params prm{};
-  cudaStream_t s = nullptr;
-  int nset = 0, nwork = 0, dtype = 0;
+  cudaStream_t s = nullptr;         // the driver's stream (capture origin)
+  std::vector<cudaStream_t> ss;     // one stream per set
+  std::vector<cudaEvent_t> ev_join;  // end of a set's captured step
+  std::vector<cudaEvent_t> ev_done;  // end of a set's host-driven work
+  cudaEvent_t ev_prod = nullptr;    // end of the batched product
+  int nset = 0, nwork = 0, dtype = 0, device = 0, nthreads = 1;
   size_t smem = 0;
   int64_t D = 0;
   int q = 0, mb = 0;
   void* shared = nullptr;  // V_k and W of all sets, set-major
   void* tables = nullptr;  // DevH<T>[nset], DevG<T>[nset]
   std::map<int, cudaGraphExec_t> graphs;
-  int graph_replays = 0;
+  std::vector<int> rc;
+  std::vector<std::string> msg;
+  clock::time_point t_start;
+  double ms_steps = 0, ms_between = 0;
 
   ~BatchDriver() {
     if (s) cudaStreamSynchronize(s);
+    for (cudaStream_t x : ss)
+      if (x) cudaStreamSynchronize(x);
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     for (auto* S : sets) delete S;
+    for (cudaEvent_t e : ev_join)
+      if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : ev_done)
+      if (e) cudaEventDestroy(e);
+    if (ev_prod) cudaEventDestroy(ev_prod);
+    for (cudaStream_t x : ss)
+      if (x) cudaStreamDestroy(x);
     if (shared) cudaFree(shared);
     if (tables) cudaFree(tables);
   }
 
+  static double ms_since(clock::time_point t) {
+    return std::chrono::duration<double, std::milli>(clock::now() - t).count();
+  }
+
+  // f(i) for every set i in [i0, nset) still without error, on up to
+  // nthreads host threads (the caller's among them).  Each thread binds the
+  // caller's device; a failure is kept in rc[i] with its message in msg[i]
+  // (error messages are per thread).
+  template <typename F>
+  void for_sets(int i0, F f) {
+    std::atomic<int> next{i0};
+    auto work = [&] {
+      cudaSetDevice(device);
+      for (int i; (i = next.fetch_add(1)) < nset;) {
+        if (rc[i] != TRBL_OK) continue;
+        rc[i] = f(i);
+        if (rc[i] != TRBL_OK) msg[i] = trbl_last_error();
+      }
+    };
+    std::vector<std::thread> th;
+    const int nt = std::min(nthreads, nset - i0);
+    for (int t = 1; t < nt; ++t) {
+      try {
+        th.emplace_back(work);
+      } catch (...) {
+        break;  // fewer threads: the others take the work
+      }
+    }
+    work();
+    for (auto& t : th) t.join();
+  }
+
+  // Set i's setup and start block on its own stream.
+  int setup_set(const trbl_hamiltonian* h, int i) {
+    Solver<T>* S = sets[i];
+    const size_t dq = size_t(D) * q;
+    T* V0 = static_cast<T*>(shared);
+    S->h = h;
+    S->p = &prm;
+    S->s = ss[i];
+    S->skip_warmup = i > 0;
+    TRY(S->setup());
+    S->Vk = V0 + dq * i;
+    S->W = V0 + dq * nset + dq * i;
+    TRY(S->init());
+    TRBL_CUDA(cudaEventRecord(ev_done[i], ss[i]));
+    return TRBL_OK;
+  }
+
   int setup(const trbl_hamiltonian* const* hs) {
+    t_start = clock::now();
     const trbl_basis* b = hs[0]->b;
     D = b->D;
     q = prm.q;
@@ -832,6 +912,19 @@ struct BatchDriver {
       smem = std::max(smem, grouped_smem_bytes(hs[i], dtype));
     }
     nwork = hs[0]->g32.nwork;
+    TRBL_CUDA(cudaGetDevice(&device));
+    nthreads = int(std::max(1u, std::min(16u, std::thread::hardware_concurrency())));
+    rc.assign(nset, TRBL_OK);
+    msg.assign(nset, std::string());
+    ss.assign(nset, nullptr);
+    ev_join.assign(nset, nullptr);
+    ev_done.assign(nset, nullptr);
+    for (int i = 0; i < nset; ++i) {
+      TRBL_CUDA(cudaStreamCreateWithFlags(&ss[i], cudaStreamNonBlocking));
+      TRBL_CUDA(cudaEventCreateWithFlags(&ev_join[i], cudaEventDisableTiming));
+      TRBL_CUDA(cudaEventCreateWithFlags(&ev_done[i], cudaEventDisableTiming));
+    }
+    TRBL_CUDA(cudaEventCreateWithFlags(&ev_prod, cudaEventDisableTiming));
     const size_t dq = size_t(D) * q;
     TRBL_CUDA(cudaMalloc(&shared, sizeof(T) * dq * 2 * nset));
     TRBL_CUDA(cudaMalloc(&tables, (sizeof(DevH<T>) + sizeof(DevG<T>)) * nset));
@@ -849,31 +942,35 @@ struct BatchDriver {
     TRBL_CUDA(cudaMemcpy(tables, hv.data(), sizeof(DevH<T>) * nset, cudaMemcpyHostToDevice));
     TRBL_CUDA(cudaMemcpy(static_cast<char*>(tables) + sizeof(DevH<T>) * nset, gv.data(), sizeof(DevG<T>) * nset,
                          cudaMemcpyHostToDevice));
-    T* V0 = static_cast<T*>(shared);
-    T* W0 = V0 + dq * nset;
     for (int i = 0; i < nset; ++i) {
       auto* S = new (std::nothrow) Solver<T>{};
       if (!S) return fail(TRBL_ERR_OOM, "host allocation failed");
       sets.push_back(S);
-      S->h = hs[i];
-      S->p = &prm;
-      S->s = s;
-      S->skip_warmup = i > 0;
-      TRY(S->setup());
-      S->Vk = V0 + dq * i;
-      S->W = W0 + dq * i;
-      TRY(S->init());
     }
+    // set 0 first: it loads the eigensolver's kernel variants for all sets
+    rc[0] = setup_set(hs[0], 0);
+    if (rc[0] != TRBL_OK) return rc[0];
+    for_sets(1, [&](int i) { return setup_set(hs[i], i); });
+    for (int i = 0; i < nset; ++i)
+      if (rc[i] != TRBL_OK) return fail(rc[i], "batched solve, set %d: %s", i, msg[i].c_str());
+    trace("batch setup: %d sets, %.1f ms", nset, ms_since(t_start));
     return TRBL_OK;
   }
 
-  // batched product for all sets, then each set's device step
+  // Batched product on s, then each set's device step on its own stream,
+  // joined back into s.
   int enqueue(bool append) {
     T* V0 = static_cast<T*>(shared);
     const size_t dq = size_t(D) * q;
     TRY(launch_grouped_batch(tables, static_cast<char*>(tables) + sizeof(DevH<T>) * nset, nset, nwork, smem, V0, q,
                              int64_t(dq), V0 + dq * nset, q, int64_t(dq), q, dtype, s));
-    for (auto* S : sets) TRY(S->step_device(append));
+    TRBL_CUDA(cudaEventRecord(ev_prod, s));
+    for (int i = 0; i < nset; ++i) {
+      TRBL_CUDA(cudaStreamWaitEvent(ss[i], ev_prod, 0));
+      TRY(sets[i]->step_device(append));
+      TRBL_CUDA(cudaEventRecord(ev_join[i], ss[i]));
+      TRBL_CUDA(cudaStreamWaitEvent(s, ev_join[i], 0));
+    }
     return TRBL_OK;
   }
 
@@ -885,11 +982,11 @@ struct BatchDriver {
     }
     cudaGraph_t g = nullptr;
     TRBL_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    const int rc = enqueue(append);
+    const int r = enqueue(append);
     const cudaError_t e = cudaStreamEndCapture(s, &g);
-    if (rc) {
+    if (r) {
       if (g) cudaGraphDestroy(g);
-      return rc;
+      return r;
     }
     TRBL_CUDA(e);
     cudaGraphExec_t ex = nullptr;
@@ -903,13 +1000,8 @@ struct BatchDriver {
 
   int run(double* evals, double* resid, void* evecs, int* status, trbl_stats* st) {
     const int nev = prm.nev;
-    const int check_every = prm.check_every > 0 ? prm.check_every : std::max(1, 32 / q);
     const int max_iter = prm.max_iter > 0 ? prm.max_iter : 100000;
-    std::vector<int> rc(nset, TRBL_OK);
-    cudaEvent_t t0, t1;
-    TRBL_CUDA(cudaEventCreate(&t0));
-    TRBL_CUDA(cudaEventCreate(&t1));
-    TRBL_CUDA(cudaEventRecord(t0, s));
+    double since_check = 0, last_check = 0;
     int it = 0;
     for (; it < max_iter; ++it) {
       bool all = true;
@@ -917,52 +1009,76 @@ struct BatchDriver {
       if (all) break;
       const int nb = sets[0]->nb;
       const bool append = nb + q <= mb;
+      const auto t0 = clock::now();
+      for (int i = 0; i < nset; ++i) TRBL_CUDA(cudaStreamWaitEvent(s, ev_done[i], 0));
       if (it == 0) {
         TRY(enqueue(append));  // eager first step: lazily configured kernels set up outside capture
       } else {
         cudaGraphExec_t ex;
         TRY(graph_for(nb, append, &ex));
         TRBL_CUDA(cudaGraphLaunch(ex, s));
-        ++graph_replays;
       }
       TRBL_CUDA(cudaStreamSynchronize(s));
-      for (int i = 0; i < nset; ++i) {
-        if (rc[i] != TRBL_OK) continue;
-        rc[i] = sets[i]->step_after(append, check_every, max_iter);
+      const double t_step = ms_since(t0);
+      ms_steps += t_step;
+      since_check += t_step;
+      // all sets test at the same steps: every check_every steps, or (adaptive)
+      // once the steps since the last test took as long as that test did
+      const bool due = prm.check_every > 0 ? (it + 1) % prm.check_every == 0 : since_check >= last_check;
+      const bool check = due || !append;
+      const auto t1 = clock::now();
+      for_sets(0, [&](int i) {
+        TRY(sets[i]->step_after(append, check, max_iter));
+        TRBL_CUDA(cudaEventRecord(ev_done[i], ss[i]));
+        return TRBL_OK;
+      });
+      const double t_between = ms_since(t1);
+      ms_between += t_between;
+      if (check) {
+        last_check = t_between;
+        since_check = 0;
       }
+      trace("batch step %d nb %d: steps %.2f ms, between %.2f ms%s", it, nb, t_step, t_between, check ? " (test)" : "");
     }
+    std::vector<char> failed(nset);
+    for (int i = 0; i < nset; ++i) failed[i] = rc[i] != TRBL_OK;
+    for_sets(0, [&](int i) {
+      const int r = sets[i]->finish(evals + size_t(i) * nev, resid ? resid + size_t(i) * nev : nullptr,
+                                    evecs ? static_cast<T*>(evecs) + size_t(i) * D * nev : nullptr, nullptr);
+      const cudaError_t e = cudaStreamSynchronize(ss[i]);
+      if (r == TRBL_OK && e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize (batched finish)");
+      return r;
+    });
+    int worst = TRBL_OK, first = -1, nbad = 0, conv = 0;
     for (int i = 0; i < nset; ++i) {
-      Solver<T>* S = sets[i];
-      if (rc[i] == TRBL_OK) {
-        const int r = S->finish(evals + size_t(i) * nev, resid ? resid + size_t(i) * nev : nullptr,
-                                evecs ? static_cast<T*>(evecs) + size_t(i) * D * nev : nullptr, nullptr);
-        rc[i] = r;
-      } else {
+      if (failed[i])
         for (int k = 0; k < nev; ++k) evals[size_t(i) * nev + k] = NAN;
-      }
       if (status) status[i] = rc[i];
-    }
-    TRBL_CUDA(cudaEventRecord(t1, s));
-    TRBL_CUDA(cudaStreamSynchronize(s));
-    int worst = TRBL_OK, conv = 0;
-    for (int i = 0; i < nset; ++i) {
-      if (rc[i] != TRBL_OK && worst == TRBL_OK) worst = rc[i];
+      if (rc[i] != TRBL_OK) {
+        ++nbad;
+        if (first < 0) {
+          first = i;
+          worst = rc[i];
+        }
+      }
       conv += sets[i]->conv;
     }
     if (st) {
       *st = trbl_stats{};
-      float tot = 0.f;
-      cudaEventElapsedTime(&tot, t0, t1);
       st->iterations = it;
       st->restarts = sets[0]->restarts;
       st->converged = conv;
       st->status = worst;
       st->normH = sets[0]->normH;
-      st->ms_total = tot;
+      st->ms_total = ms_since(t_start);
+      st->ms_apply = ms_steps;
+      st->ms_ritz = ms_between;
     }
-    cudaEventDestroy(t0);
-    cudaEventDestroy(t1);
-    if (worst != TRBL_OK) return fail(worst, "batched solve: %d of %d sets did not finish cleanly", int(std::count_if(rc.begin(), rc.end(), [](int x) { return x != TRBL_OK; })), nset);
+    trace("batch: %d steps, steps %.1f ms, between %.1f ms, total %.1f ms", it, ms_steps, ms_between,
+          ms_since(t_start));
+    if (worst != TRBL_OK)
+      return fail(worst, "batched solve: %d of %d sets did not finish cleanly; set %d: %s", nbad, nset, first,
+                  msg[first].c_str());
     return TRBL_OK;
   }
 };
