@@ -170,6 +170,26 @@ int trbl_param_count(const trbl_basis* b, int64_t* n);
 int trbl_grad(const trbl_hamiltonian* h, const void* X, int64_t ldx, int nvec, int dtype, double* dtheta,
               int64_t nparams, void* stream);
 
+/* trbl_block_dot on the tensor cores (TRBL_PROJ_TENSOR arithmetic) for
+ * FP32 data: same arguments, layout and errors, with dtype TRBL_F32 only,
+ * q <= 32, B and W 16-byte aligned and ldb, ldw multiples of 4
+ * (TRBL_ERR_ARG otherwise). */
+int trbl_block_dot_tc(const void* B, int64_t ldb, int m, const void* W, int64_t ldw, int q, int64_t D, double* C,
+                      void* stream);
+
+/* Block update Out[:, 0:n] = alpha * In[:, 0:K] U + beta * Out over D rows:
+ * the "W := W - V_k alpha_k" and reorthogonalisation updates of Alg. 3/4
+ * (Sec. III C/D) and W R^-1 of the block QR.  In, Out: device, row-major,
+ * leading dimensions ldi >= K and ldo >= n, dtype TRBL_F32 or TRBL_F64, must
+ * not overlap; U: device FP64 K x n row-major (ld ldu >= n).  algo:
+ * TRBL_PROJ_TENSOR or TRBL_PROJ_CUDA_CORE (FP32 data; FP64 data ignore it);
+ * the tensor-core form needs n <= 32, In 16-byte aligned with ldi a multiple
+ * of 4, and falls back to the CUDA cores otherwise.  Allocates stream-ordered
+ * scratch (cudaMallocAsync) for the tensor-core form.  Asynchronous on
+ * stream.  Errors: TRBL_ERR_ARG, TRBL_ERR_OOM, TRBL_ERR_CUDA. */
+int trbl_block_update(const void* In, int64_t ldi, int K, const double* U, int64_t ldu, int n, void* Out,
+                      int64_t ldo, int64_t D, double alpha, double beta, int dtype, int algo, void* stream);
+
 /* Allocation-free form of trbl_block_dot, for callers that must not
  * allocate device memory during the call: code running where the CUDA
  * allocator may not be entered (inside host callbacks, or while another
@@ -195,6 +215,17 @@ int trbl_grad(const trbl_hamiltonian* h, const void* X, int64_t ldx, int nvec, i
 int trbl_block_dot_noalloc(const void* B, int64_t ldb, int m, const void* W, int64_t ldw, int q, int64_t D,
                            int dtype, double* C, void* stream);
 
+/* Arithmetic of the FP32 block projections C = B^T W and updates
+ * Out = alpha In U + beta Out (mixed precision).  TRBL_PROJ_TENSOR: tcgen05
+ * tensor-core MMAs on split TF32 operands (x = hi + lo with TF32 hi and lo,
+ * |x - hi - lo| <= 2^-22 |x|; a b formed as a_hi b_hi + a_hi b_lo + a_lo b_hi
+ * in FP32; projections drain to FP64 every 2,048 rows), for q or n <= 32
+ * and 16-byte aligned row-major operands, other shapes falling back to the
+ * CUDA cores.  TRBL_PROJ_CUDA_CORE: FP32 FMAs on the CUDA cores with FP64
+ * combination of row chunks.  FP64 data always use FP64 FMAs. */
+#define TRBL_PROJ_TENSOR 0
+#define TRBL_PROJ_CUDA_CORE 1
+
 #define TRBL_PREC_F64 1   /* FP64 vectors, apply and projections */
 #define TRBL_PREC_MIXED 2 /* FP32 vectors and apply; FP64 CGS2 coefficients, CholQR2, Ritz */
 
@@ -213,6 +244,8 @@ typedef struct trbl_params {
                           have taken at least as long as that test did */
   uint64_t seed;       /* start block: uniform(-1,1) from splitmix64(seed<<32 + i*q + j) */
   double normH;        /* ||H|| used by tol; 0 = estimated by the solver (largest |Ritz value|) */
+  int projections;     /* TRBL_PROJ_TENSOR (0, default) or TRBL_PROJ_CUDA_CORE: how the FP32
+                          projections and updates of mixed precision are computed */
 } trbl_params;
 
 /* Per-solve statistics (per-phase times mirror the paper's Fig. 5(c)). */

@@ -12,12 +12,12 @@ App. B).
 """
 from ._lib import (  # noqa: F401
     TRBL_OK, TRBL_ERR_ARG, TRBL_ERR_CUDA, TRBL_ERR_OOM, TRBL_ERR_BREAKDOWN, TRBL_ERR_NOCONV,
-    TRBL_F32, TRBL_F64, TRBL_PREC_F64, TRBL_PREC_MIXED, TrblError,
+    TRBL_F32, TRBL_F64, TRBL_PREC_F64, TRBL_PREC_MIXED, TRBL_PROJ_TENSOR, TRBL_PROJ_CUDA_CORE, TrblError,
     lib, library_path,
     trbl_basis_create, trbl_basis_destroy, trbl_basis_info, trbl_basis_export,
     trbl_basis_export_jumps, trbl_hamiltonian_create, trbl_hamiltonian_destroy,
     trbl_apply_block, trbl_solve, trbl_last_error, trbl_kernel_launches, trbl_block_dot, block_dot,
-    trbl_block_dot_noalloc,
+    trbl_block_dot_noalloc, trbl_block_dot_tc, trbl_block_update, block_update,
     trbl_solver_create, trbl_solver_step, trbl_solver_step_host, trbl_solver_block,
     trbl_solver_stats, trbl_solver_destroy,
     trbl_param_count, trbl_grad, arrays_from_theta, clusters_of, hf_gradient, LowestEigenvalues,

@@ -13,6 +13,7 @@ from . import build as _build
 TRBL_OK, TRBL_ERR_ARG, TRBL_ERR_CUDA, TRBL_ERR_OOM, TRBL_ERR_BREAKDOWN, TRBL_ERR_NOCONV = range(6)
 TRBL_F32, TRBL_F64 = 0, 1
 TRBL_PREC_F64, TRBL_PREC_MIXED = 1, 2
+TRBL_PROJ_TENSOR, TRBL_PROJ_CUDA_CORE = 0, 1
 
 
 class TrblError(RuntimeError):
@@ -34,7 +35,8 @@ class trbl_basis_sizes(C.Structure):
 class trbl_params(C.Structure):
     _fields_ = [("nev", C.c_int), ("q", C.c_int), ("max_basis", C.c_int), ("keep", C.c_int),
                 ("tol", C.c_double), ("precision", C.c_int), ("max_iter", C.c_int),
-                ("check_every", C.c_int), ("seed", C.c_uint64), ("normH", C.c_double)]
+                ("check_every", C.c_int), ("seed", C.c_uint64), ("normH", C.c_double),
+                ("projections", C.c_int)]
 
 
 class trbl_stats(C.Structure):
@@ -84,6 +86,9 @@ def lib():
         "trbl_block_dot": (C.c_int, [_VP, C.c_int64, C.c_int, _VP, C.c_int64, C.c_int, C.c_int64, C.c_int, _VP, _VP]),
         "trbl_block_dot_noalloc": (C.c_int, [_VP, C.c_int64, C.c_int, _VP, C.c_int64, C.c_int, C.c_int64, C.c_int,
                                              _VP, _VP]),
+        "trbl_block_dot_tc": (C.c_int, [_VP, C.c_int64, C.c_int, _VP, C.c_int64, C.c_int, C.c_int64, _VP, _VP]),
+        "trbl_block_update": (C.c_int, [_VP, C.c_int64, C.c_int, _VP, C.c_int64, C.c_int, _VP, C.c_int64,
+                                        C.c_int64, C.c_double, C.c_double, C.c_int, C.c_int, _VP]),
         "trbl_param_count": (C.c_int, [_VP, C.POINTER(C.c_int64)]),
         "trbl_grad": (C.c_int, [_VP, _VP, C.c_int64, C.c_int, C.c_int, _DP, C.c_int64, _VP]),
         "trbl_solve_batch": (C.c_int, [C.POINTER(_VP), C.c_int, C.POINTER(trbl_params), _DP, _DP, _VP,
@@ -203,17 +208,47 @@ def trbl_block_dot_noalloc(B_ptr: int, ldb: int, m: int, W_ptr: int, ldw: int, q
                                         C_ptr, stream))
 
 
-def block_dot(B, W, stream=None):
-    """C = B^T W (FP64, m x q) for torch CUDA tensors B (D x m) and W (D x q)."""
+def trbl_block_dot_tc(B_ptr: int, ldb: int, m: int, W_ptr: int, ldw: int, q: int, D: int, C_ptr: int,
+                      stream: int = 0):
+    _check(lib().trbl_block_dot_tc(B_ptr, int(ldb), int(m), W_ptr, int(ldw), int(q), int(D), C_ptr, stream))
+
+
+def trbl_block_update(In_ptr: int, ldi: int, K: int, U_ptr: int, ldu: int, n: int, Out_ptr: int, ldo: int, D: int,
+                      alpha: float, beta: float, dtype: int, algo: int, stream: int = 0):
+    _check(lib().trbl_block_update(In_ptr, int(ldi), int(K), U_ptr, int(ldu), int(n), Out_ptr, int(ldo), int(D),
+                                   float(alpha), float(beta), int(dtype), int(algo), stream))
+
+
+def block_dot(B, W, stream=None, tensor_cores=False):
+    """C = B^T W (FP64, m x q) for torch CUDA tensors B (D x m) and W (D x q);
+    tensor_cores=True uses trbl_block_dot_tc (FP32 data only)."""
     import torch
     if B.dtype != W.dtype or B.stride(1) != 1 or W.stride(1) != 1 or B.shape[0] != W.shape[0]:
         raise ValueError("B and W must share dtype and rows, with unit column stride")
     dt = TRBL_F64 if B.dtype == torch.float64 else TRBL_F32
     C = torch.empty((B.shape[1], W.shape[1]), dtype=torch.float64, device=B.device)
     s = stream if stream is not None else torch.cuda.current_stream(B.device)
-    trbl_block_dot(B.data_ptr(), B.stride(0), B.shape[1], W.data_ptr(), W.stride(0), W.shape[1], B.shape[0], dt,
-                   C.data_ptr(), s.cuda_stream)
+    if tensor_cores:
+        trbl_block_dot_tc(B.data_ptr(), B.stride(0), B.shape[1], W.data_ptr(), W.stride(0), W.shape[1], B.shape[0],
+                          C.data_ptr(), s.cuda_stream)
+    else:
+        trbl_block_dot(B.data_ptr(), B.stride(0), B.shape[1], W.data_ptr(), W.stride(0), W.shape[1], B.shape[0], dt,
+                       C.data_ptr(), s.cuda_stream)
     return C
+
+
+def block_update(In, U, Out, alpha=-1.0, beta=1.0, algo=TRBL_PROJ_TENSOR, stream=None):
+    """Out = alpha * In U + beta * Out in place (In: D x K, U: K x n FP64, Out:
+    D x n, torch CUDA tensors with unit column stride); returns Out."""
+    import torch
+    if In.dtype != Out.dtype or In.stride(1) != 1 or Out.stride(1) != 1 or In.shape[0] != Out.shape[0]:
+        raise ValueError("In and Out must share dtype and rows, with unit column stride")
+    U = U.to(device=In.device, dtype=torch.float64).contiguous()
+    dt = TRBL_F64 if In.dtype == torch.float64 else TRBL_F32
+    s = stream if stream is not None else torch.cuda.current_stream(In.device)
+    trbl_block_update(In.data_ptr(), In.stride(0), In.shape[1], U.data_ptr(), U.stride(0), U.shape[1],
+                      Out.data_ptr(), Out.stride(0), In.shape[0], alpha, beta, dt, algo, s.cuda_stream)
+    return Out
 
 
 def trbl_solve(h: int, params: trbl_params, evals_ptr, resid_ptr, evecs_ptr: int,
@@ -289,12 +324,12 @@ class Hamiltonian:
 def solve(h: Hamiltonian, nev: int, q: int, max_basis: int, tol: float,
           precision: int = TRBL_PREC_F64, keep: int = 0, max_iter: int = 0,
           check_every: int = 0, seed: int = 1, normH: float = 0.0, want_vectors: bool = True,
-          stream=None, raise_on_noconv: bool = True):
+          stream=None, raise_on_noconv: bool = True, projections: int = TRBL_PROJ_TENSOR):
     """Lowest nev eigenpairs by trbl_solve.  Returns (evals, resid, evecs or None, stats dict)."""
     import torch
     D = h.basis.dim
     p = trbl_params(int(nev), int(q), int(max_basis), int(keep), float(tol), int(precision),
-                    int(max_iter), int(check_every), int(seed), float(normH))
+                    int(max_iter), int(check_every), int(seed), float(normH), int(projections))
     st = trbl_stats()
     ev = np.zeros(nev)
     rs = np.zeros(nev)
@@ -313,9 +348,9 @@ def solve(h: Hamiltonian, nev: int, q: int, max_basis: int, tol: float,
 
 
 def _params(nev, q, max_basis, tol, precision=TRBL_PREC_F64, keep=0, max_iter=0, check_every=0, seed=1,
-            normH=0.0):
+            normH=0.0, projections=TRBL_PROJ_TENSOR):
     return trbl_params(int(nev), int(q), int(max_basis), int(keep), float(tol), int(precision),
-                       int(max_iter), int(check_every), int(seed), float(normH))
+                       int(max_iter), int(check_every), int(seed), float(normH), int(projections))
 
 
 def trbl_solver_create(h: int, params: trbl_params, stream: int = 0) -> int:
@@ -358,14 +393,14 @@ class Solver:
 
     def __init__(self, h: Hamiltonian, nev: int, q: int, max_basis: int, tol: float,
                  precision: int = TRBL_PREC_F64, keep: int = 0, check_every: int = 0, seed: int = 1,
-                 normH: float = 0.0, stream=None):
+                 normH: float = 0.0, stream=None, projections: int = TRBL_PROJ_TENSOR):
         import torch
         self.h = h
         self.nev, self.q, self.precision = nev, q, precision
         self.handle = None
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
-        self.params = _params(nev, q, max_basis, tol, precision, keep, 0, check_every, seed, normH)
+        self.params = _params(nev, q, max_basis, tol, precision, keep, 0, check_every, seed, normH, projections)
         self.handle = trbl_solver_create(h.handle, self.params, s.cuda_stream)
 
     def step(self) -> int:
@@ -539,14 +574,15 @@ class LowestEigenvalues:
 
 def solve_batch(hs, nev: int, q: int, max_basis: int, tol: float, precision: int = TRBL_PREC_F64,
                 keep: int = 0, max_iter: int = 0, check_every: int = 0, seed: int = 1, normH: float = 0.0,
-                want_vectors: bool = False, want_resid: bool = True, stream=None):
+                want_vectors: bool = False, want_resid: bool = True, stream=None,
+                projections: int = TRBL_PROJ_TENSOR):
     """trbl_solve_batch over Hamiltonians sharing one basis.  Returns
     (evals [nset, nev], resid [nset, nev] or None, vectors [nset, D, nev] or
     None, per-set status, stats dict)."""
     import torch
     nset = len(hs)
     D = hs[0].basis.dim
-    p = _params(nev, q, max_basis, tol, precision, keep, max_iter, check_every, seed, normH)
+    p = _params(nev, q, max_basis, tol, precision, keep, max_iter, check_every, seed, normH, projections)
     arr = (_VP * nset)(*[h.handle for h in hs])
     ev = np.zeros((nset, nev))
     rs = np.zeros((nset, nev)) if want_resid else None

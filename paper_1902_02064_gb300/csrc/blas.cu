@@ -370,6 +370,10 @@ int block_dot(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, in
               Workspace& ws, cudaStream_t s) {
   if (m <= 0) return TRBL_OK;
   if constexpr (std::is_same<T, float>::value) {
+    if (ws.tensor) {
+      const int rc = block_dot_tc(B, ldb, m, W, ldw, q, D, C, ws.partial, ws.partial_bytes, ws.sm_count, s);
+      if (rc != -1) return rc;
+    }
     const int rc = block_dot_tma(B, ldb, m, W, ldw, q, D, C, ws.partial, ws.partial_bytes, ws.sm_count, s);
     if (rc != -1) return rc;
   }
@@ -443,6 +447,18 @@ int rowgemm(const T* In, int64_t ldi, int K, const double* U, int64_t ldu, int n
   return TRBL_OK;
 }
 
+template <typename T>
+int rowgemm_ws(const T* In, int64_t ldi, int K, const double* U, int64_t ldu, int n, T* Out, int64_t ldo, int64_t D,
+               double alpha, double beta, Workspace& ws, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (ws.tensor && n > 0 && D > 0 && K > 0) {
+      const int rc = rowgemm_tc(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta, ws.ut, ws.ut_bytes, s);
+      if (rc != -1) return rc;
+    }
+  }
+  return rowgemm<T>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta, s);
+}
+
 template <typename S, typename T>
 int copy_cols(const S* src, int64_t lds, T* dst, int64_t ldd, int64_t D, int ncol, cudaStream_t s) {
   if (ncol <= 0 || D <= 0) return TRBL_OK;
@@ -472,6 +488,8 @@ template int block_dot<float>(const float*, int64_t, int, const float*, int64_t,
 template int block_dot<double>(const double*, int64_t, int, const double*, int64_t, int, int64_t, double*, Workspace&, cudaStream_t);
 template int rowgemm<float>(const float*, int64_t, int, const double*, int64_t, int, float*, int64_t, int64_t, double, double, cudaStream_t);
 template int rowgemm<double>(const double*, int64_t, int, const double*, int64_t, int, double*, int64_t, int64_t, double, double, cudaStream_t);
+template int rowgemm_ws<float>(const float*, int64_t, int, const double*, int64_t, int, float*, int64_t, int64_t, double, double, Workspace&, cudaStream_t);
+template int rowgemm_ws<double>(const double*, int64_t, int, const double*, int64_t, int, double*, int64_t, int64_t, double, double, Workspace&, cudaStream_t);
 template int copy_cols<float, float>(const float*, int64_t, float*, int64_t, int64_t, int, cudaStream_t);
 template int copy_cols<double, double>(const double*, int64_t, double*, int64_t, int64_t, int, cudaStream_t);
 template int copy_cols<float, double>(const float*, int64_t, double*, int64_t, int64_t, int, cudaStream_t);

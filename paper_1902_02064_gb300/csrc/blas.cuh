@@ -10,6 +10,9 @@ struct Workspace {
   double* partial = nullptr;  // block_dot partial sums
   size_t partial_bytes = 0;
   int sm_count = 152;
+  float* ut = nullptr;        // rowgemm_tc: split transpose of U
+  size_t ut_bytes = 0;
+  bool tensor = false;        // FP32 projections on the tensor cores when shapes allow
 };
 
 // Bytes of Workspace::partial needed by block_dot with these m, q.
@@ -44,6 +47,22 @@ int tma_error_to_host(int* host, cudaStream_t s);
 int block_dot_tma(const float* B, int64_t ldb, int m, const float* W, int64_t ldw, int q, int64_t D, double* C,
                   double* partial, size_t partial_bytes, int sm_count, cudaStream_t s);
 int dot_error_to_host(int* host, cudaStream_t s);
+
+// rowgemm through the workspace: FP32 data with ws.tensor set go to the
+// tensor-core kernel when the shapes allow, else as rowgemm.
+template <typename T>
+int rowgemm_ws(const T* In, int64_t ldi, int K, const double* U, int64_t ldu, int n, T* Out, int64_t ldo, int64_t D,
+               double alpha, double beta, Workspace& ws, cudaStream_t s);
+
+// Tensor-core (tcgen05, split TF32) forms for FP32 data, n / q <= 32
+// (proj_tc.cu); -1 when the shapes, alignment or workspace do not allow them.
+int block_dot_tc(const float* B, int64_t ldb, int m, const float* W, int64_t ldw, int q, int64_t D, double* C,
+                 double* partial, size_t partial_bytes, int sm_count, cudaStream_t s);
+size_t rowgemm_tc_workspace_bytes(int K);
+int rowgemm_tc(const float* In, int64_t ldi, int K, const double* U, int64_t ldu, int n, float* Out, int64_t ldo,
+               int64_t D, double alpha, double beta, float* ut, size_t ut_bytes, cudaStream_t s);
+// Enqueues a copy of the tensor-core kernels' wait-timeout word to host memory.
+int tc_error_to_host(int* host, cudaStream_t s);
 
 // dst[:, 0:ncol] = src[:, 0:ncol] (with type conversion).
 template <typename S, typename T>

@@ -315,9 +315,9 @@ struct Solver {
     TRY(block_dot<T>(basis, mb, nb, Wb, q, q, D, C, ws, s));
     if (Cout_first && Cout_first != C)
       TRBL_CUDA(cudaMemcpyAsync(Cout_first, C, sizeof(double) * nb * q, cudaMemcpyDeviceToDevice, s));
-    TRY(rowgemm<T>(basis, mb, nb, C, q, q, Wb, q, D, -1.0, 1.0, s));
+    TRY(rowgemm_ws<T>(basis, mb, nb, C, q, q, Wb, q, D, -1.0, 1.0, ws, s));
     TRY(block_dot<T>(basis, mb, nb, Wb, q, q, D, C + size_t(mb) * q, ws, s));
-    TRY(rowgemm<T>(basis, mb, nb, C + size_t(mb) * q, q, q, Wb, q, D, -1.0, 1.0, s));
+    TRY(rowgemm_ws<T>(basis, mb, nb, C + size_t(mb) * q, q, q, Wb, q, D, -1.0, 1.0, ws, s));
     return TRBL_OK;
   }
 
@@ -325,10 +325,8 @@ struct Solver {
   // deficient columns found in pass 1 (their flags stay in hflags).
   int cholqr2(T* Win, double thresh_abs, double thresh_rel, double thresh_max, int* ndef) {
     TRY(cholqr2_async(Win, thresh_abs, thresh_rel, thresh_max));
-    TRY(tma_error_to_host(hflags + kTmaErr, s));
-    TRY(dot_error_to_host(hflags + kTmaErr + 1, s));
     TRBL_CUDA(cudaStreamSynchronize(s));
-    if (hflags[kTmaErr] || hflags[kTmaErr + 1]) return fail(TRBL_ERR_CUDA, "a TMA wait in a projection timed out");
+    TRY(wait_errors());
     *ndef = hflags[kF1] + hflags[kF2];
     return TRBL_OK;
   }
@@ -340,14 +338,25 @@ struct Solver {
     chol_kernel<<<1, 64, 0, s>>>(G, q, thresh_abs, thresh_rel, thresh_max, R1, R1i, flags + kF1); note_launch();
     TRBL_CUDA(cudaGetLastError());
     TRBL_CUDA(cudaMemcpyAsync(hflags + kF1, flags + kF1, sizeof(int) * (q + 1), cudaMemcpyDeviceToHost, s));
-    TRY(rowgemm<T>(Win, q, q, R1i, q, q, W2, q, D, 1.0, 0.0, s));
+    TRY(rowgemm_ws<T>(Win, q, q, R1i, q, q, W2, q, D, 1.0, 0.0, ws, s));
     TRY(block_dot<T>(W2, q, q, W2, q, q, D, G, ws, s));
     chol_kernel<<<1, 64, 0, s>>>(G, q, 0.0, 1e-3, 0.0, R2, R2i, flags + kF2); note_launch();
     TRBL_CUDA(cudaGetLastError());
     TRBL_CUDA(cudaMemcpyAsync(hflags + kF2, flags + kF2, sizeof(int), cudaMemcpyDeviceToHost, s));
-    TRY(rowgemm<T>(W2, q, q, R2i, q, q, Vk, q, D, 1.0, 0.0, s));
+    TRY(rowgemm_ws<T>(W2, q, q, R2i, q, q, Vk, q, D, 1.0, 0.0, ws, s));
     upper_mul_kernel<<<(q * q + 127) / 128, 128, 0, s>>>(R2, R1, q, beta); note_launch();
     TRBL_CUDA(cudaGetLastError());
+    // wait-timeout words of the TMA and tensor-core kernels, read by wait_errors()
+    TRY(tma_error_to_host(hflags + kTmaErr, s));
+    TRY(dot_error_to_host(hflags + kTmaErr + 1, s));
+    TRY(tc_error_to_host(hflags + kTmaErr + 2, s));
+    return TRBL_OK;
+  }
+
+  // After the stream synchronised past cholqr2_async.
+  int wait_errors() {
+    if (hflags[kTmaErr] || hflags[kTmaErr + 1] || hflags[kTmaErr + 2])
+      return fail(TRBL_ERR_CUDA, "a bounded wait in a projection kernel timed out");
     return TRBL_OK;
   }
 
@@ -562,6 +571,7 @@ struct Solver {
   // After step_device ran (stream synchronised): deficiency check, Rayleigh-
   // Ritz when due, and the thick restart when the basis was full.
   int step_after(bool appended, bool check_due, int max_iter) {
+    TRY(wait_errors());
     if (hflags[kF1] + hflags[kF2] > 0)
       return fail(TRBL_ERR_BREAKDOWN, "batched step: rank-deficient block (the batched driver has no repair path)");
     ++iter;
@@ -712,6 +722,7 @@ struct Solver {
       HXd = ar.take<double>(dq);
       rpart = ar.take<double>(size_t(nchunk_res) * q);
       rtrue = ar.take<double>(mb);
+      ws.ut = ar.take<float>(rowgemm_tc_workspace_bytes(mb) / sizeof(float));
       ws.partial = ar.take<double>(ws.partial_bytes / sizeof(double));
       flags = ar.take<int>(kFlagInts);
       if (pass == 0) {
@@ -726,6 +737,8 @@ struct Solver {
       }
     }
     devinfo = flags + kInfo;
+    ws.ut_bytes = rowgemm_tc_workspace_bytes(mb);
+    ws.tensor = p->projections == TRBL_PROJ_TENSOR;
     trace("workspace %.3f GB at %p", ar.cap / 1e9, ar.base);
     if (cusolverDnCreate(&sol) != CUSOLVER_STATUS_SUCCESS) return fail(TRBL_ERR_CUDA, "cusolverDnCreate failed");
     TRBL_SOLVER(cusolverDnSetStream(sol, s));
