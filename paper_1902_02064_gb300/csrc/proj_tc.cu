@@ -6,23 +6,29 @@
 //
 // Precision: every FP32 operand value x is split into TF32 parts
 // x = hi + lo (|x - hi - lo| <= 2^-22 |x|), and a product a b is formed as
-// a_hi b_hi + a_hi b_lo + a_lo b_hi (three MMAs into one FP32 accumulator
-// in tensor memory); the dropped a_lo b_lo is below 2^-22 |a b|.  The
+// a_hi b_hi + a_hi b_lo + a_lo b_hi (MMAs into FP32 accumulators in tensor
+// memory, summed when read out); the dropped a_lo b_lo is below 2^-22 |a b|.  The
 // projection drains its accumulator into FP64 registers every 64 stages
 // (2,048 rows), so FP32 sums never run over more than 2,048 rows; row
 // chunks are then combined in FP64 in a fixed order.
 //
-// Pipeline of one thread block (256 threads): thread 0 streams 32-row
-// stages of the operands by TMA (128-byte swizzle) into a ring of four raw
-// stages; all threads convert a raw stage into split K-major operand tiles
-// (a transpose for the projection, whose operands are row-major in K) in one
-// of two conversion buffers; thread 0 then issues the stage's MMAs and
-// commits them to an mbarrier that frees the conversion buffer.  Waits are
-// bounded (tma.cuh): a timeout sets an error word the solver reads at its
-// next synchronisation, and the block waits (bounded) for its copies and
-// MMAs in flight before it frees its tensor memory.  Shared memory (over
-// 160 KB) admits one such block per SM, so the 32 tensor-memory columns a
-// block allocates are always available.
+// Warp-specialised pipeline of one thread block (320 threads), chained by
+// mbarriers only:
+// * warp 0 (one lane) streams 32-row stages of the operands by TMA
+//   (128-byte swizzle) into a ring of four raw stages;
+// * warps 2-9 (256 threads) convert a raw stage into split K-major operand
+//   tiles (a transpose for the projection, whose operands are row-major in
+//   K) in one of three conversion buffers, then release the raw stage;
+// * warp 1 (one lane) issues the stage's MMAs and commits them to an
+//   mbarrier that frees the conversion buffer;
+// * two accumulators in tensor memory alternate between segments (the
+//   projection's 64-stage drains) or output tiles (the update), so the
+//   converter warps read one out while the MMAs fill the other.
+// Waits are bounded (tma.cuh): a timeout sets an error word the solver
+// reads at its next synchronisation, and the block waits (bounded) for its
+// copies and MMAs in flight before it frees its tensor memory.  Shared
+// memory (over 200 KB) admits one such block per SM, so the 128
+// tensor-memory columns a block allocates are always available.
 #include <cuda.h>
 
 #include <algorithm>
@@ -38,14 +44,19 @@ void reduce_partials(const double* partial, int nchunk, int mq, double* C, cudaS
 
 namespace {
 
-constexpr int kThreadsTC = 256;
+constexpr int kConvWarps = 8;
+constexpr int kThreadsTC = 64 + 32 * kConvWarps;  // producer warp, MMA warp, converter warps
 constexpr int kRawStages = 4;
-constexpr int kDrain = 64;          // projection stages between FP64 drains
+constexpr int kDrain = 64;          // projection stages per accumulator segment
 constexpr int kTile = 128;          // MMA M: columns of B (projection) or rows of In (update)
-constexpr int kN = 32;              // MMA N
+constexpr int kN = 32;              // MMA N (one accumulator = 32 tensor-memory columns)
+constexpr int kConvBufs = 3;
+constexpr uint32_t kTmemCols = 128;  // two accumulators of 64 columns (hi*hi + lo*hi | hi*lo)
 constexpr uint32_t kIdesc = idesc_tf32(kTile, kN);
+constexpr uint32_t kIdesc2 = idesc_tf32(kTile, 2 * kN);
 constexpr int kBox = 32 * 32 * 4;   // 32 x 32 FP32 box, 4 KB
 constexpr int kTileBytes = kTile * 128;  // 128 rows of 128 bytes, 16 KB
+constexpr int kConvBytes = 2 * kTileBytes + 2 * kBox;  // A hi, A lo, B hi, B lo
 
 __device__ int g_tc_err = 0;
 
@@ -85,23 +96,29 @@ __device__ __forceinline__ void transpose_split(const unsigned char* box, unsign
   }
 }
 
-// Issues the three split MMAs of each of the four K steps of a stage.
-__device__ __forceinline__ void issue_split_mmas(uint32_t tmem, const unsigned char* ahi, const unsigned char* alo,
-                                                 const unsigned char* bhi, const unsigned char* blo, bool first) {
-  const uint64_t dah = sdesc_k128(ahi), dal = sdesc_k128(alo), dbh = sdesc_k128(bhi), dbl = sdesc_k128(blo);
+// Issues the split MMAs of the four K steps of a stage.  B's hi and lo
+// tiles are adjacent (rows 0-31 hi, 32-63 lo), so one N = 64 MMA forms
+// a_hi b_hi (accumulator columns 0-31) and a_hi b_lo (columns 32-63) with
+// one read of a_hi; a second, N = 32, adds a_lo b_hi into columns 0-31.
+__device__ __forceinline__ void issue_split_mmas(uint32_t acc, const unsigned char* cv, bool first) {
+  const uint64_t dah = sdesc_k128(cv), dal = sdesc_k128(cv + kTileBytes);
+  const uint64_t db = sdesc_k128(cv + 2 * kTileBytes);
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk) {
     const uint64_t o = uint64_t(2 * kk);  // +32 bytes in the start-address field
-    mma_tf32(tmem, dah + o, dbh + o, kIdesc, (first && kk == 0) ? 0u : 1u);
-    mma_tf32(tmem, dah + o, dbl + o, kIdesc, 1u);
-    mma_tf32(tmem, dal + o, dbh + o, kIdesc, 1u);
+    mma_tf32(acc, dah + o, db + o, kIdesc2, (first && kk == 0) ? 0u : 1u);
+    mma_tf32(acc, dal + o, db + o, kIdesc, 1u);
   }
 }
 
 struct TcShared {
-  uint64_t full[kRawStages];  // raw stage landed (TMA)
-  uint64_t mdone[2];          // conversion buffer's MMAs completed
-  uint32_t tmem;              // tensor-memory base address
+  uint64_t full[kRawStages];   // raw stage landed (TMA bytes)
+  uint64_t empty[kRawStages];  // raw stage converted (one arrival per converter warp)
+  uint64_t cfull[kConvBufs];   // conversion buffer written (per converter warp)
+  uint64_t mdone[kConvBufs];   // conversion buffer's MMAs completed (commit)
+  uint64_t accfull[2];         // accumulator's MMAs completed (commit)
+  uint64_t accfree[2];         // accumulator read out (per converter warp)
+  uint32_t tmem;               // tensor-memory base address
   int abort;
 };
 
@@ -109,16 +126,36 @@ __device__ __forceinline__ unsigned char* align1024(unsigned char* p) {
   return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
 }
 
+__device__ __forceinline__ bool aborted(const TcShared& sh) { return *reinterpret_cast<const volatile int*>(&sh.abort); }
+__device__ __forceinline__ void set_abort(TcShared& sh) { *reinterpret_cast<volatile int*>(&sh.abort) = 1; }
+
+// Bounded wait; a timeout stops the whole block.
+__device__ __forceinline__ bool wait_or_abort(TcShared& sh, uint64_t* bar, uint32_t parity) {
+  if (mbar_wait(bar, parity, &g_tc_err)) return true;
+  set_abort(sh);
+  return false;
+}
+
 __device__ __forceinline__ void tc_setup(TcShared& sh, int warp) {
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kRawStages; ++s) mbar_init(&sh.full[s], 1);
-    for (int b = 0; b < 2; ++b) mbar_init(&sh.mdone[b], 1);
+    for (int s = 0; s < kRawStages; ++s) {
+      mbar_init(&sh.full[s], 1);
+      mbar_init(&sh.empty[s], kConvWarps);
+    }
+    for (int b = 0; b < kConvBufs; ++b) {
+      mbar_init(&sh.cfull[b], kConvWarps);
+      mbar_init(&sh.mdone[b], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sh.accfull[b], 1);
+      mbar_init(&sh.accfree[b], kConvWarps);
+    }
     fence_barrier_init();
     sh.abort = 0;
   }
   __syncwarp();
   if (warp == 0) {
-    tmem_alloc(&sh.tmem, 32);
+    tmem_alloc(&sh.tmem, kTmemCols);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -126,43 +163,67 @@ __device__ __forceinline__ void tc_setup(TcShared& sh, int warp) {
   tc_fence_after();
 }
 
-__device__ __forceinline__ void tc_teardown(TcShared& sh, int warp) {
+// Whole block, after every role has left its loop.  After a timeout, the
+// producer lane waits (bounded) for the copies that may still be in flight
+// (only the last kRawStages issued: an earlier slot was refilled, so its
+// copy had been consumed) and the MMA lane for its last commit, before the
+// tensor memory is freed.
+__device__ __forceinline__ void tc_finish(TcShared& sh, int warp, int lane, int64_t issued, int64_t committed) {
+  __syncthreads();
+  if (aborted(sh)) {
+    if (warp == 0 && lane == 0)
+      for (int64_t jj = std::max<int64_t>(0, issued - kRawStages); jj < issued; ++jj)
+        mbar_wait(&sh.full[jj % kRawStages], uint32_t((jj / kRawStages) & 1), nullptr);
+    if (warp == 1 && lane == 0 && committed >= 0)
+      mbar_wait(&sh.mdone[committed % kConvBufs], uint32_t((committed / kConvBufs) & 1), nullptr);
+  }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(sh.tmem, 32);
+    tmem_dealloc(sh.tmem, kTmemCols);
   }
+}
+
+// Converter warps: signal that this warp's part of a buffer is written
+// (stores made visible to the tensor core first).
+__device__ __forceinline__ void warp_arrive_async(uint64_t* bar, int lane) {
+  fence_async_smem();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(bar);
+}
+
+// This converter thread's 16 accumulator values (its lane's row, its warp's
+// column half): the sum of the a_hi b_hi + a_lo b_hi and a_hi b_lo columns of
+// accumulator a.  The warp index mod 4 selects the 32 tensor-memory lanes a
+// warp may read.
+__device__ __forceinline__ void acc_load(uint32_t tmem, int warp, int a, float (&v)[16]) {
+  const uint32_t base = tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(a * 2 * kN + 16 * ((warp - 2) >> 2));
+  float w[16];
+  tmem_ld16(base, v);
+  tmem_ld16(base + kN, w);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] += w[i];
 }
 
 }  // namespace
 
 namespace {
 
-constexpr int kConvBytes = 2 * kTileBytes + 2 * kBox;  // A hi, A lo, B hi, B lo
-
-// Waits (bounded) for the copies still in flight and the last committed
-// MMAs of a block that gives up, so that it can free its tensor memory and
-// exit safely.
-__device__ void tc_drain_after_abort(TcShared& sh, int64_t j, int64_t issued, int64_t committed) {
-  for (int64_t jj = j; jj < issued; ++jj)
-    mbar_wait(&sh.full[jj % kRawStages], uint32_t((jj / kRawStages) & 1), nullptr);
-  if (committed >= 0) mbar_wait(&sh.mdone[committed & 1], uint32_t((committed >> 1) & 1), nullptr);
-}
-
 // FP64 partial sums of C = B^T W: blockIdx.x = 128-column tile of B,
 // blockIdx.y = row chunk (rows_per_chunk rows, a multiple of 32).  The MMA's
 // rows are B's columns (M = 128), its columns W's (N = 32), K runs over the
-// chunk's rows.  Raw stage: 4 boxes of B (32 rows x 32 columns) and one of
-// W; conversion transposes them into K-major split tiles.
+// chunk's rows.  Raw stage j: 4 boxes of B (32 rows x 32 columns) and one of
+// W; conversion transposes them into K-major split tiles in buffer j mod 3.
+// Accumulator segment g (stages 64 g .. 64 g + 63) uses accumulator g & 1.
 __global__ void __launch_bounds__(kThreadsTC, 1)
     block_dot_tc_kernel(const __grid_constant__ CUtensorMap tb, const __grid_constant__ CUtensorMap tw, int m, int q,
                         int64_t D, int64_t rows_per_chunk, double* __restrict__ partial) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = align1024(smem_raw);
   unsigned char* raw = base;                              // [kRawStages][5 boxes]
-  unsigned char* conv = base + kRawStages * 5 * kBox;     // [2][kConvBytes]
-  TcShared& sh = *reinterpret_cast<TcShared*>(conv + 2 * kConvBytes);
+  unsigned char* conv = base + kRawStages * 5 * kBox;     // [kConvBufs][kConvBytes]
+  TcShared& sh = *reinterpret_cast<TcShared*>(conv + kConvBufs * kConvBytes);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * kTile;
   const int nbox = std::min(4, (m - m0 + 31) / 32);
@@ -171,79 +232,93 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   const int64_t njobs = r_end > r_begin ? (r_end - r_begin + 31) / 32 : 0;
   tc_setup(sh, warp);
   const uint32_t tmem = sh.tmem;
-  const uint32_t stage_bytes = uint32_t(nbox + 1) * kBox;
-  auto issue = [&](int64_t j) {
-    const int s = int(j % kRawStages);
-    unsigned char* st = raw + s * 5 * kBox;
-    const int y = int(r_begin + j * 32);
-    mbar_expect_tx(&sh.full[s], stage_bytes);
-    for (int b = 0; b < nbox; ++b) tma_load_2d(st + b * kBox, &tb, m0 + 32 * b, y, &sh.full[s]);
-    tma_load_2d(st + 4 * kBox, &tw, 0, y, &sh.full[s]);
-  };
   int64_t issued = 0, committed = -1;
-  if (tid == 0)
-    for (; issued < std::min<int64_t>(kRawStages, njobs); ++issued) issue(issued);
-  // conversion role: box mybox, micro-block (rb, cb) of it (see transpose_split)
-  const int P = tid >> 3, a = tid & 7;
-  const int rb = a, cb = ((P & 1) << 2) + (((a >> 1) + ((P >> 1) & 3)) & 3);
-  const int mybox = P >> 3;
   double acc[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) acc[i] = 0.0;
-  bool first = true;
-  int64_t j = 0;
-  for (; j < njobs; ++j) {
-    const int s = int(j % kRawStages), c = int(j & 1);
-    bool ok = mbar_wait(&sh.full[s], uint32_t((j / kRawStages) & 1), &g_tc_err);
-    if (j >= 2) ok = mbar_wait(&sh.mdone[c], uint32_t(((j - 2) >> 1) & 1), &g_tc_err) && ok;
-    if (!ok) sh.abort = 1;
-    const unsigned char* st = raw + s * 5 * kBox;
-    unsigned char* cv = conv + c * kConvBytes;
-    const int valid = int(std::min<int64_t>(32, r_end - (r_begin + j * 32)));
-    if (ok) {
+
+  if (warp == 0) {
+    // ---- TMA producer ----
+    if (lane == 0) {
+      const uint32_t stage_bytes = uint32_t(nbox + 1) * kBox;
+      for (int64_t j = 0; j < njobs; ++j) {
+        const int s = int(j % kRawStages);
+        if (j >= kRawStages && !wait_or_abort(sh, &sh.empty[s], uint32_t((j / kRawStages - 1) & 1))) break;
+        if (aborted(sh)) break;
+        unsigned char* st = raw + s * 5 * kBox;
+        const int y = int(r_begin + j * 32);
+        mbar_expect_tx(&sh.full[s], stage_bytes);
+        for (int b = 0; b < nbox; ++b) tma_load_2d(st + b * kBox, &tb, m0 + 32 * b, y, &sh.full[s]);
+        tma_load_2d(st + 4 * kBox, &tw, 0, y, &sh.full[s]);
+        issued = j + 1;
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      for (int64_t j = 0; j < njobs; ++j) {
+        const int c = int(j % kConvBufs);
+        const int64_t g = j / kDrain;
+        const int a = int(g & 1);
+        const bool seg_first = j % kDrain == 0;
+        if (seg_first && g >= 2 && !wait_or_abort(sh, &sh.accfree[a], uint32_t(((g - 2) >> 1) & 1))) break;
+        if (!wait_or_abort(sh, &sh.cfull[c], uint32_t((j / kConvBufs) & 1))) break;
+        if (aborted(sh)) break;
+        tc_fence_after();
+        issue_split_mmas(tmem + uint32_t(a * 2 * kN), conv + c * kConvBytes, seg_first);
+        mma_commit(&sh.mdone[c]);
+        if (j % kDrain == kDrain - 1 || j == njobs - 1) mma_commit(&sh.accfull[a]);
+        committed = j;
+      }
+    }
+  } else {
+    // ---- converters ----
+    const int ct = tid - 64;
+    const int P = ct >> 3, a8 = ct & 7;
+    const int rb = a8, cb = ((P & 1) << 2) + (((a8 >> 1) + ((P >> 1) & 3)) & 3);
+    const int mybox = P >> 3;
+    for (int64_t j = 0; j < njobs; ++j) {
+      const int s = int(j % kRawStages), c = int(j % kConvBufs);
+      if (!wait_or_abort(sh, &sh.full[s], uint32_t((j / kRawStages) & 1))) break;
+      if (j >= kConvBufs && !wait_or_abort(sh, &sh.mdone[c], uint32_t((j / kConvBufs - 1) & 1))) break;
+      if (aborted(sh)) break;
+      const unsigned char* st = raw + s * 5 * kBox;
+      unsigned char* cv = conv + c * kConvBytes;
+      const int valid = int(std::min<int64_t>(32, r_end - (r_begin + j * 32)));
       if (mybox < nbox)
         transpose_split(st + mybox * kBox, cv + mybox * kBox, cv + kTileBytes + mybox * kBox, rb, cb, valid);
-      if (tid < 64) transpose_split(st + 4 * kBox, cv + 2 * kTileBytes, cv + 2 * kTileBytes + kBox, rb, cb, valid);
-    }
-    fence_async_smem();
-    __syncthreads();
-    if (sh.abort) break;
-    if (tid == 0) {
-      if (issued < njobs) issue(issued++);
-      tc_fence_after();
-      issue_split_mmas(tmem, cv, cv + kTileBytes, cv + 2 * kTileBytes, cv + 2 * kTileBytes + kBox, first);
-      mma_commit(&sh.mdone[c]);
-      first = false;
-    }
-    committed = j;
-    if ((j + 1) % kDrain == 0 || j == njobs - 1) {
-      // move the FP32 accumulator into FP64 registers and restart it
-      if (!mbar_wait(&sh.mdone[c], uint32_t((j >> 1) & 1), &g_tc_err)) sh.abort = 1;
-      tc_fence_after();
-      float v[16];
-      tmem_ld16(tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(16 * (warp >> 2)), v);
+      if (ct < 64) transpose_split(st + 4 * kBox, cv + 2 * kTileBytes, cv + 2 * kTileBytes + kBox, rb, cb, valid);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh.empty[s]);
+      warp_arrive_async(&sh.cfull[c], lane);
+      if (j % kDrain == kDrain - 1 || j == njobs - 1) {
+        // segment done: move its accumulator into FP64 registers
+        const int64_t g = j / kDrain;
+        const int a = int(g & 1);
+        if (!wait_or_abort(sh, &sh.accfull[a], uint32_t((g >> 1) & 1))) break;
+        tc_fence_after();
+        float v[16];
+        acc_load(tmem, warp, a, v);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) acc[i] += double(v[i]);
-      tc_fence_before();
-      __syncthreads();
-      if (sh.abort) break;
-      first = true;
+        for (int i = 0; i < 16; ++i) acc[i] += double(v[i]);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh.accfree[a]);
+      }
     }
   }
-  if (sh.abort) {
-    if (tid == 0) tc_drain_after_abort(sh, j, issued, committed);
-    tc_teardown(sh, warp);
-    return;
-  }
-  double* Pp = partial + int64_t(blockIdx.y) * m * q;
-  const int i = m0 + 32 * (warp & 3) + lane;
-  const int c0 = 16 * (warp >> 2);
-  if (i < m) {
+  const bool ok = !aborted(sh);
+  tc_finish(sh, warp, lane, issued, committed);
+  if (warp >= 2 && ok && !aborted(sh)) {
+    double* Pp = partial + int64_t(blockIdx.y) * m * q;
+    const int i = m0 + 32 * (warp & 3) + lane;
+    const int c0 = 16 * ((warp - 2) >> 2);
+    if (i < m) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
-      if (c0 + k < q) Pp[int64_t(i) * q + c0 + k] = acc[k];
+      for (int k = 0; k < 16; ++k)
+        if (c0 + k < q) Pp[int64_t(i) * q + c0 + k] = acc[k];
+    }
   }
-  tc_teardown(sh, warp);
 }
 
 // U (K x n, FP64, row-major) as TF32 parts of its transpose for the update's
@@ -261,12 +336,41 @@ __global__ void ut_split_kernel(const double* __restrict__ U, int64_t ldu, int K
   ut[int64_t(32 + j) * Kp + k] = lo;
 }
 
+// Epilogue of one 128-row output tile held in accumulator a: this converter
+// thread's row, 16 of the 32 columns.
+__device__ __forceinline__ void update_epilogue(TcShared& sh, uint32_t tmem, int warp, int lane, int a, int64_t t,
+                                                int64_t tile, float* __restrict__ Out, int64_t ldo, int64_t D, int n,
+                                                float alpha, float beta) {
+  if (!wait_or_abort(sh, &sh.accfull[a], uint32_t((t >> 1) & 1))) return;
+  tc_fence_after();
+  float v[16];
+  acc_load(tmem, warp, a, v);
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&sh.accfree[a]);
+  const int64_t r = tile * kTile + 32 * (warp & 3) + lane;
+  const int c0 = 16 * ((warp - 2) >> 2);
+  if (r < D && c0 < n) {
+    float* o = Out + r * ldo + c0;
+    const int nc = std::min(16, n - c0);
+    float old[16];
+    // all loads of the row first: one memory latency per tile, not one per column
+#pragma unroll
+    for (int k = 0; k < 16; ++k) old[k] = (beta != 0.f && k < nc) ? o[k] : 0.f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (k < nc) o[k] = fmaf(beta, old[k], alpha * v[k]);
+  }
+}
+
 // Out = alpha In U + beta Out for persistent blocks striding over 128-row
 // tiles of In; the MMA's rows are In's rows (M = 128), its columns U's
 // (N = 32), K runs over In's columns in stages of 32.  Raw stage: one In box
 // (32 columns x 128 rows, already K-major) and one box of U's split
 // transpose (32 columns x 64 rows: hi, then lo); conversion splits In into
-// hi and lo tiles of the same layout and copies U's parts.
+// hi and lo tiles of the same layout and copies U's parts.  The block's
+// t-th tile uses accumulator t & 1; its epilogue runs after the converters
+// have converted the next stage, so it overlaps the tile's last MMAs.
 __global__ void __launch_bounds__(kThreadsTC, 1)
     rowgemm_tc_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tu, int K, int n,
                       float* __restrict__ Out, int64_t ldo, int64_t D, float alpha, float beta) {
@@ -274,8 +378,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = align1024(smem_raw);
   unsigned char* raw = base;                                // [kRawStages][kRawBytes]
-  unsigned char* conv = base + kRawStages * kRawBytes;      // [2][kConvBytes]
-  TcShared& sh = *reinterpret_cast<TcShared*>(conv + 2 * kConvBytes);
+  unsigned char* conv = base + kRawStages * kRawBytes;      // [kConvBufs][kConvBytes]
+  TcShared& sh = *reinterpret_cast<TcShared*>(conv + kConvBufs * kConvBytes);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t ntiles = (D + kTile - 1) / kTile;
   const int nk = (K + 31) / 32;
@@ -283,32 +387,57 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   const int64_t njobs = my_tiles * nk;
   tc_setup(sh, warp);
   const uint32_t tmem = sh.tmem;
-  auto issue = [&](int64_t j) {
-    const int s = int(j % kRawStages);
-    unsigned char* st = raw + s * kRawBytes;
-    const int64_t ti = blockIdx.x + (j / nk) * gridDim.x;
-    const int kc = int(j % nk);
-    mbar_expect_tx(&sh.full[s], uint32_t(kRawBytes));
-    tma_load_2d(st, &tin, kc * 32, int(ti * kTile), &sh.full[s]);
-    tma_load_2d(st + kTileBytes, &tu, kc * 32, 0, &sh.full[s]);
-  };
   int64_t issued = 0, committed = -1;
-  if (tid == 0)
-    for (; issued < std::min<int64_t>(kRawStages, njobs); ++issued) issue(issued);
-  int64_t j = 0;
-  for (; j < njobs; ++j) {
-    const int s = int(j % kRawStages), c = int(j & 1);
-    const int kc = int(j % nk);
-    bool ok = mbar_wait(&sh.full[s], uint32_t((j / kRawStages) & 1), &g_tc_err);
-    if (j >= 2) ok = mbar_wait(&sh.mdone[c], uint32_t(((j - 2) >> 1) & 1), &g_tc_err) && ok;
-    if (!ok) sh.abort = 1;
-    const unsigned char* st = raw + s * kRawBytes;
-    unsigned char* cv = conv + c * kConvBytes;
-    if (ok) {
+
+  if (warp == 0) {
+    // ---- TMA producer ----
+    if (lane == 0) {
+      for (int64_t j = 0; j < njobs; ++j) {
+        const int s = int(j % kRawStages);
+        if (j >= kRawStages && !wait_or_abort(sh, &sh.empty[s], uint32_t((j / kRawStages - 1) & 1))) break;
+        if (aborted(sh)) break;
+        unsigned char* st = raw + s * kRawBytes;
+        const int64_t tile = blockIdx.x + (j / nk) * gridDim.x;
+        const int kc = int(j % nk);
+        mbar_expect_tx(&sh.full[s], uint32_t(kRawBytes));
+        tma_load_2d(st, &tin, kc * 32, int(tile * kTile), &sh.full[s]);
+        tma_load_2d(st + kTileBytes, &tu, kc * 32, 0, &sh.full[s]);
+        issued = j + 1;
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      for (int64_t j = 0; j < njobs; ++j) {
+        const int c = int(j % kConvBufs);
+        const int64_t t = j / nk;
+        const int kc = int(j % nk);
+        const int a = int(t & 1);
+        if (kc == 0 && t >= 2 && !wait_or_abort(sh, &sh.accfree[a], uint32_t(((t - 2) >> 1) & 1))) break;
+        if (!wait_or_abort(sh, &sh.cfull[c], uint32_t((j / kConvBufs) & 1))) break;
+        if (aborted(sh)) break;
+        tc_fence_after();
+        issue_split_mmas(tmem + uint32_t(a * 2 * kN), conv + c * kConvBytes, kc == 0);
+        mma_commit(&sh.mdone[c]);
+        if (kc == nk - 1) mma_commit(&sh.accfull[a]);
+        committed = j;
+      }
+    }
+  } else {
+    // ---- converters (and epilogues) ----
+    const int ct = tid - 64;
+    int64_t pending = -1;  // local tile index whose epilogue is due
+    for (int64_t j = 0; j < njobs; ++j) {
+      const int s = int(j % kRawStages), c = int(j % kConvBufs);
+      if (!wait_or_abort(sh, &sh.full[s], uint32_t((j / kRawStages) & 1))) break;
+      if (j >= kConvBufs && !wait_or_abort(sh, &sh.mdone[c], uint32_t((j / kConvBufs - 1) & 1))) break;
+      if (aborted(sh)) break;
+      const unsigned char* st = raw + s * kRawBytes;
+      unsigned char* cv = conv + c * kConvBytes;
       // In: same layout in and out, 16 bytes per access (conflict-free)
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int off = (tid + u * kThreadsTC) * 16;
+        const int off = (ct + u * 256) * 16;
         const float4 x = ld4(st + off);
         float h[4], l[4];
         tf32_split(x.x, h[0], l[0]);
@@ -321,41 +450,24 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       // U's hi and lo parts (8 KB)
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        const int off = (tid + u * kThreadsTC) * 16;
+        const int off = (ct + u * 256) * 16;
         *reinterpret_cast<float4*>(cv + 2 * kTileBytes + off) = ld4(st + kTileBytes + off);
       }
-    }
-    fence_async_smem();
-    __syncthreads();
-    if (sh.abort) break;
-    if (tid == 0) {
-      if (issued < njobs) issue(issued++);
-      tc_fence_after();
-      issue_split_mmas(tmem, cv, cv + kTileBytes, cv + 2 * kTileBytes, cv + 2 * kTileBytes + kBox, kc == 0);
-      mma_commit(&sh.mdone[c]);
-    }
-    committed = j;
-    if (kc == nk - 1) {
-      // epilogue of the tile: this thread's row, 16 of the 32 columns
-      if (!mbar_wait(&sh.mdone[c], uint32_t((j >> 1) & 1), &g_tc_err)) sh.abort = 1;
-      tc_fence_after();
-      float v[16];
-      tmem_ld16(tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(16 * (warp >> 2)), v);
-      const int64_t r = (blockIdx.x + (j / nk) * gridDim.x) * kTile + 32 * (warp & 3) + lane;
-      const int c0 = 16 * (warp >> 2);
-      if (!sh.abort && r < D) {
-        float* o = Out + r * ldo + c0;
-#pragma unroll
-        for (int k = 0; k < 16; ++k)
-          if (c0 + k < n) o[k] = (beta == 0.f) ? alpha * v[k] : fmaf(beta, o[k], alpha * v[k]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh.empty[s]);
+      warp_arrive_async(&sh.cfull[c], lane);
+      if (pending >= 0) {
+        update_epilogue(sh, tmem, warp, lane, int(pending & 1), pending, blockIdx.x + pending * gridDim.x, Out, ldo,
+                        D, n, alpha, beta);
+        pending = -1;
       }
-      tc_fence_before();
-      __syncthreads();
-      if (sh.abort) break;
+      if (j % nk == nk - 1) pending = j / nk;
     }
+    if (pending >= 0 && !aborted(sh))
+      update_epilogue(sh, tmem, warp, lane, int(pending & 1), pending, blockIdx.x + pending * gridDim.x, Out, ldo, D,
+                      n, alpha, beta);
   }
-  if (sh.abort && tid == 0) tc_drain_after_abort(sh, j, issued, committed);
-  tc_teardown(sh, warp);
+  tc_finish(sh, warp, lane, issued, committed);
 }
 
 int sm_count_now() {
@@ -390,7 +502,7 @@ int block_dot_tc(const float* B, int64_t ldb, int m, const float* W, int64_t ldw
   int rc = make_tmap_2d_f32(&tb, B, uint64_t(m), uint64_t(D), uint64_t(ldb), 32, 32);
   if (!rc) rc = make_tmap_2d_f32(&tw, W, uint64_t(q), uint64_t(D), uint64_t(ldw), 32, 32);
   if (rc) return rc;
-  const size_t smem = size_t(kRawStages) * 5 * kBox + 2 * size_t(kConvBytes) + sizeof(TcShared) + 1024;
+  const size_t smem = size_t(kRawStages) * 5 * kBox + kConvBufs * size_t(kConvBytes) + sizeof(TcShared) + 1024;
   static const cudaError_t cfg =
       cudaFuncSetAttribute(block_dot_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   TRBL_CUDA(cfg);
@@ -417,7 +529,7 @@ int rowgemm_tc(const float* In, int64_t ldi, int K, const double* U, int64_t ldu
   int rc = make_tmap_2d_f32(&tin, In, uint64_t(K), uint64_t(D), uint64_t(ldi), 32, kTile);
   if (!rc) rc = make_tmap_2d_f32(&tu, ut, uint64_t(Kp), 64, uint64_t(Kp), 32, 64);
   if (rc) return rc;
-  const size_t smem = size_t(kRawStages) * (kTileBytes + 2 * kBox) + 2 * size_t(kConvBytes) + sizeof(TcShared) + 1024;
+  const size_t smem = size_t(kRawStages) * (kTileBytes + 2 * kBox) + kConvBufs * size_t(kConvBytes) + sizeof(TcShared) + 1024;
   static const cudaError_t cfg =
       cudaFuncSetAttribute(rowgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   TRBL_CUDA(cfg);
