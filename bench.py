@@ -385,6 +385,11 @@ def run_ours(args, rank, world):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes, "ms_per_step": el / args.steps * 1e3},
     }
+    if rank == 0 and world == 1 and not args.no_proj:
+        del sv
+        sv = None
+        torch.cuda.empty_cache()
+        line["projections"] = projections_at(trbl, D, 640, q, peak)
     if rank == 0 and world == 1 and not args.no_ttn:
         line["time_to_nev"] = time_to_nev(trbl)
     if rank == 0 and world == 1 and not args.no_batch:
@@ -396,6 +401,44 @@ def run_ours(args, rank, world):
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def projections_at(trbl, D, m, q, peak, reps=5):
+    """The solver's two dense contractions alone at the workload's size, m
+    stored vectors (C = B^T W, W -= B C; FP32 data): tensor-core (tcgen05,
+    split TF32) and CUDA-core forms, CUDA-event timed, with the fraction of
+    the measured HBM bandwidth (bytes 4 D (m + q) and 4 D (m + 2q))."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    B = torch.rand((D, m), generator=g, device="cuda") * 2 - 1
+    W = torch.rand((D, q), generator=g, device="cuda") * 2 - 1
+    U = (torch.rand((m, q), generator=g, device="cuda", dtype=torch.float64) * 2 - 1) / m
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    calls = {"dot_tensor": (lambda: trbl.block_dot(B, W, tensor_cores=True), 4 * D * (m + q)),
+             "dot_cuda_core": (lambda: trbl.block_dot(B, W), 4 * D * (m + q)),
+             "update_tensor": (lambda: trbl.block_update(B, U, W, -1.0, 1.0, algo=trbl.TRBL_PROJ_TENSOR),
+                               4 * D * (m + 2 * q)),
+             "update_cuda_core": (lambda: trbl.block_update(B, U, W, -1.0, 1.0, algo=trbl.TRBL_PROJ_CUDA_CORE),
+                                  4 * D * (m + 2 * q))}
+    out = {"dim": D, "m": m, "q": q, "inputs": "B %.1f GB (larger than L2)" % (4 * D * m / 1e9),
+           "kernels": "block_dot_tc_kernel, rowgemm_tc_kernel (tcgen05 kind::tf32, split operands)",
+           "ncu": "profiles/proj_tc_D1M_m640_q32.md"}
+    for name, (f, nbytes) in calls.items():
+        f()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            f()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "gbs": gbs, "frac_of_hbm": gbs / peak}
+    del B, W, U
+    torch.cuda.empty_cache()
+    return out
 
 
 def time_to_nev(trbl, name="s12_4p4n"):
@@ -424,6 +467,37 @@ def time_to_nev(trbl, name="s12_4p4n"):
                       "max_abs_eig_err_over_normH": float(np.abs(ev - ref).max() / normH),
                       "max_true_resid_over_normH": float(np.nanmax(rs) / normH),
                       "phase_ms": {k: st[k] for k in ("ms_apply", "ms_orth", "ms_qr", "ms_ritz", "ms_restart")}}
+    return out
+
+
+def time_to_nev_large(trbl, name, arms):
+    """Full solves of a large workload to residual 1e-6 ||H|| (no stored
+    oracle eigenvalues at this size): each arm's eigenvalues are compared
+    with the first arm's, and every arm reports its true residuals (FP64
+    apply).  arms: (label, precision, q) tuples."""
+    import torch
+    w, sa, sb, inter = synth.workload(name)
+    tb = trbl.Basis(sa, w.nA, sb, w.nB, w.twoM)
+    th = trbl.Hamiltonian.from_interaction(tb, inter)
+    out = {"workload": name, "dim": tb.dim, "nev": w.nev, "max_basis": w.max_basis, "tol_rel_normH": 1e-6}
+    first = None
+    for label, prec, q in arms:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev, rs, X, st = trbl.solve(th, w.nev, q, w.max_basis, 1e-6, precision=prec, want_vectors=False,
+                                   raise_on_noconv=False, max_iter=20000)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        r = {"seconds": el, "q": q, "converged": st["converged"], "rc": st["rc"], "iterations": st["iterations"],
+             "restarts": st["restarts"], "normH": st["normH"],
+             "max_true_resid_over_normH": float(np.nanmax(rs) / st["normH"]),
+             "phase_ms": {k: st[k] for k in ("ms_apply", "ms_orth", "ms_qr", "ms_ritz", "ms_restart")}}
+        if first is None:
+            first = ev
+        else:
+            r["max_abs_eig_diff_vs_first_arm_over_normH"] = float(np.abs(ev - first).max() / st["normH"])
+        out[label] = r
+        print(json.dumps({label: r}), file=sys.stderr, flush=True)
     return out
 
 
@@ -467,6 +541,39 @@ def gradient_batch(trbl, nset=64):
             "sets_ok": int(sum(1 for x in status if x == 0)), "graph_steps": st["iterations"],
             "max_eig_diff_batch_vs_single_over_normH": max_diff / st["normH"],
             "max_euler_identity_error_over_normH": euler}
+
+
+def run_proj_only(args):
+    """Time the block projection C = B^T W and the update W -= B U alone (FP32
+    data; tensor-core and CUDA-core forms) for D, m, q given as "D,m,q"."""
+    import torch
+    import paper_1902_02064_gb300 as trbl
+    D, m, q = (int(x) for x in args.proj_only.split(","))
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    B = torch.rand((D, m), generator=g, device="cuda") * 2 - 1
+    W = torch.rand((D, q), generator=g, device="cuda") * 2 - 1
+    U = (torch.rand((m, q), generator=g, device="cuda", dtype=torch.float64) * 2 - 1) / m
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    calls = {"dot_tc": lambda: trbl.block_dot(B, W, tensor_cores=True),
+             "dot_cc": lambda: trbl.block_dot(B, W),
+             "update_tc": lambda: trbl.block_update(B, U, W, -1.0, 1.0, algo=trbl.TRBL_PROJ_TENSOR),
+             "update_cc": lambda: trbl.block_update(B, U, W, -1.0, 1.0, algo=trbl.TRBL_PROJ_CUDA_CORE)}
+    out = {"D": D, "m": m, "q": q}
+    for name, f in calls.items():
+        for _ in range(args.warmup):
+            f()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            f()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        nbytes = 4 * D * (m + q) if name.startswith("dot") else 4 * D * (m + 2 * q)
+        out[name] = {"ms": ms, "gbs": nbytes / (ms * 1e-3) / 1e9}
+    print(json.dumps(out), flush=True)
 
 
 def run_apply_only(args):
@@ -516,7 +623,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttn", action="store_true", help="skip the time-to-nev solves")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-set gradient batch")
+    ap.add_argument("--no-proj", action="store_true", help="skip the projection kernels' own timing")
+    ap.add_argument("--ttn-large", metavar="WORKLOAD", default=None,
+                    help="only: time to nev eigenpairs at 1e-6 ||H|| on a large workload (s20_4p4n: mixed, "
+                         "FP64 block and FP64 q = 1 arms; s20_5p5n: mixed) and print one JSON line")
     ap.add_argument("--apply-only", default=None, help="time only W = H V on this workload")
+    ap.add_argument("--proj-only", default=None, metavar="D,m,q",
+                    help="time only the block projection and update (FP32, both forms) at these sizes")
     ap.add_argument("--workload", default=WORKLOAD, help="workload of the solver steps (default: the 5+5 space)")
     ap.add_argument("--q", type=int, default=0)
     ap.add_argument("--fp64", action="store_true")
@@ -525,6 +638,17 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.apply_only:
         run_apply_only(args)
+    elif args.proj_only:
+        run_proj_only(args)
+    elif args.ttn_large:
+        import paper_1902_02064_gb300 as trbl
+        w = synth.WORKLOADS[args.ttn_large]
+        if args.ttn_large == "s20_5p5n":
+            arms = (("mixed_q%d" % w.q, trbl.TRBL_PREC_MIXED, w.q),)
+        else:
+            arms = (("fp64_q%d" % w.q, trbl.TRBL_PREC_F64, w.q), ("mixed_q%d" % w.q, trbl.TRBL_PREC_MIXED, w.q),
+                    ("fp64_q1", trbl.TRBL_PREC_F64, 1))
+        print(json.dumps({"time_to_nev": time_to_nev_large(trbl, args.ttn_large, arms)}), flush=True)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -221,7 +221,8 @@ int trbl_block_dot_noalloc(const void* B, int64_t ldb, int m, const void* W, int
  * |x - hi - lo| <= 2^-22 |x|; a b formed as a_hi b_hi + a_hi b_lo + a_lo b_hi
  * in FP32; projections drain to FP64 every 2,048 rows), for q or n <= 32
  * and 16-byte aligned row-major operands, other shapes falling back to the
- * CUDA cores.  TRBL_PROJ_CUDA_CORE: FP32 FMAs on the CUDA cores with FP64
+ * CUDA cores.  The solver sends updates with K < 256 to the CUDA cores,
+ * which are faster there.  TRBL_PROJ_CUDA_CORE: FP32 FMAs on the CUDA cores with FP64
  * combination of row chunks.  FP64 data always use FP64 FMAs. */
 #define TRBL_PROJ_TENSOR 0
 #define TRBL_PROJ_CUDA_CORE 1

@@ -296,7 +296,9 @@ int dot_launch(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, i
   const int mtiles = (m + MT - 1) / MT;
   const int target = 4 * ws.sm_count;
   int64_t nchunk = (target + mtiles - 1) / mtiles;
-  const int64_t max_chunks = (D + RS - 1) / RS;
+  // at least kMinChunkRows rows per block: a small problem then leaves SMs
+  // free for the projections of other problems running beside it
+  const int64_t max_chunks = std::max<int64_t>(1, std::min<int64_t>((D + RS - 1) / RS, D / kMinChunkRows));
   if (nchunk > max_chunks) nchunk = max_chunks;
   if (nchunk < 1) nchunk = 1;
   int64_t rows = (D + nchunk - 1) / nchunk;
@@ -451,7 +453,7 @@ template <typename T>
 int rowgemm_ws(const T* In, int64_t ldi, int K, const double* U, int64_t ldu, int n, T* Out, int64_t ldo, int64_t D,
                double alpha, double beta, Workspace& ws, cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
-    if (ws.tensor && n > 0 && D > 0 && K > 0) {
+    if (ws.tensor && n > 0 && D > 0 && K > 0 && K >= ws.tc_min_k) {
       const int rc = rowgemm_tc(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta, ws.ut, ws.ut_bytes, s);
       if (rc != -1) return rc;
     }

@@ -13,7 +13,13 @@ struct Workspace {
   float* ut = nullptr;        // rowgemm_tc: split transpose of U
   size_t ut_bytes = 0;
   bool tensor = false;        // FP32 projections on the tensor cores when shapes allow
+  int tc_min_k = 1;           // rowgemm_ws: smallest K sent to the tensor cores
 };
+
+// Smallest row chunk of a block of the solver's projections (block_dot):
+// problems of a few thousand rows take few SMs and leave the rest to
+// problems running beside them (batched solves).
+constexpr int64_t kMinChunkRows = 512;
 
 // Bytes of Workspace::partial needed by block_dot with these m, q.
 size_t block_dot_workspace_bytes(int m, int q, int sm_count);

@@ -20,6 +20,7 @@
 // threshold (an exhausted Krylov direction) is replaced by a fresh seeded
 // random vector, the block is re-orthogonalised, and beta_k = V_{k+1}^T W.
 // The small symmetric eigenproblem uses cuSOLVER's syevd (FP64).
+#include <cublas_v2.h>
 #include <cusolverDn.h>
 
 #include <algorithm>
@@ -28,6 +29,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <type_traits>
+#include <climits>
 #include <cmath>
 #include <map>
 #include <atomic>
@@ -293,6 +295,9 @@ struct Solver {
   int lwork;
   int64_t nchunk_res;
   cusolverDnHandle_t sol = nullptr;
+  cublasHandle_t blas = nullptr;
+  float* Uf = nullptr;       // FP32 copy of a small coefficient matrix for cuBLAS
+  bool emulated_ok = true;   // FP32-accurate BF16-split tensor-core GEMM available
   double *hbuf;  // pinned: theta[mb], res[mb], flags as doubles
   int* hflags;
   uint64_t reseed = 0;
@@ -303,6 +308,7 @@ struct Solver {
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     if (sol) cusolverDnDestroy(sol);
+    if (blas) cublasDestroy(blas);
     if (hbuf) cudaFreeHost(hbuf);
     if (syev_work) cudaFree(syev_work);
   }
@@ -439,13 +445,44 @@ struct Solver {
     return TRBL_OK;
   }
 
+  // Out[rows x n] (row-major, ld ldo) = In[rows x K] (row-major, ld ldi) U,
+  // U FP64 K x n row-major (ld n): the dense GEMMs of the restart and of the
+  // Ritz vectors, as cuBLAS GEMMs.  FP64 data in FP64; FP32 data with cuBLAS's
+  // FP32-accurate tensor-core emulation (operands split into three BF16
+  // parts) where the library offers it, plain FP32 otherwise.
+  int gemm_rm(const T* In, int64_t ldi, int K, const double* U, int n, T* Out, int64_t ldo, int64_t rows) {
+    if (rows <= 0 || n <= 0 || K <= 0) return TRBL_OK;
+    if (rows > INT32_MAX || ldi > INT32_MAX || ldo > INT32_MAX) return fail(TRBL_ERR_ARG, "GEMM too large");
+    cublasStatus_t st;
+    if constexpr (std::is_same<T, double>::value) {
+      const double one = 1.0, zero = 0.0;
+      st = cublasDgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, n, int(rows), K, &one, U, n, In, int(ldi), &zero, Out,
+                       int(ldo));
+    } else {
+      TRY(copy_cols<double, float>(U, n, Uf, n, K, n, s));
+      const float one = 1.f, zero = 0.f;
+      st = CUBLAS_STATUS_NOT_SUPPORTED;
+      if (emulated_ok) {
+        st = cublasGemmEx(blas, CUBLAS_OP_N, CUBLAS_OP_N, n, int(rows), K, &one, Uf, CUDA_R_32F, n, In, CUDA_R_32F,
+                          int(ldi), &zero, Out, CUDA_R_32F, int(ldo), CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
+                          CUBLAS_GEMM_DEFAULT);
+        if (st == CUBLAS_STATUS_NOT_SUPPORTED) emulated_ok = false;
+      }
+      if (!emulated_ok)
+        st = cublasGemmEx(blas, CUBLAS_OP_N, CUBLAS_OP_N, n, int(rows), K, &one, Uf, CUDA_R_32F, n, In, CUDA_R_32F,
+                          int(ldi), &zero, Out, CUDA_R_32F, int(ldo), CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+    }
+    if (st != CUBLAS_STATUS_SUCCESS) return fail(TRBL_ERR_CUDA, "cuBLAS GEMM failed (status %d)", int(st));
+    return TRBL_OK;
+  }
+
   // basis[:, 0:n_out] <- basis[:, 0:nb] U[:, 0:n_out] in row panels
   int compress(int nb, int n_out) {
     transpose_kernel<<<(nb * n_out + 255) / 256, 256, 0, s>>>(Aw, mb, nb, n_out, Ut); note_launch();
     TRBL_CUDA(cudaGetLastError());
     for (int64_t r0 = 0; r0 < D; r0 += panel_rows) {
       const int64_t nr = std::min(panel_rows, D - r0);
-      TRY(rowgemm<T>(basis + r0 * mb, mb, nb, Ut, n_out, n_out, panel, n_out, nr, 1.0, 0.0, s));
+      TRY(gemm_rm(basis + r0 * mb, mb, nb, Ut, n_out, panel, n_out, nr));
       TRY(copy_cols<T, T>(panel, n_out, basis + r0 * mb, mb, nr, n_out, s));
     }
     return TRBL_OK;
@@ -631,7 +668,7 @@ struct Solver {
     for (int i = n; i < nev; ++i) evals[i] = NAN;
     transpose_kernel<<<(nr * n + 255) / 256, 256, 0, s>>>(Aw, mb, nr, n, Ut); note_launch();
     TRBL_CUDA(cudaGetLastError());
-    if (evecs) TRY(rowgemm<T>(basis, mb, nr, Ut, n, n, static_cast<T*>(evecs), nev, D, 1.0, 0.0, s));
+    if (evecs) TRY(gemm_rm(basis, mb, nr, Ut, n, static_cast<T*>(evecs), nev, D));
     if (resid) {
       // true residuals ||H x - theta x|| with an FP64 apply, q columns at a time
       const int64_t nchunk = nchunk_res;
@@ -716,6 +753,7 @@ struct Solver {
       Tm = ar.take<double>(size_t(mb) * mb);
       Aw = ar.take<double>(size_t(mb) * mb);
       Ut = ar.take<double>(size_t(mb) * mb);
+      Uf = ar.take<float>(size_t(mb) * mb);
       theta = ar.take<double>(mb);
       res = ar.take<double>(mb);
       Xd = ar.take<double>(dq);
@@ -739,9 +777,15 @@ struct Solver {
     devinfo = flags + kInfo;
     ws.ut_bytes = rowgemm_tc_workspace_bytes(mb);
     ws.tensor = p->projections == TRBL_PROJ_TENSOR;
+    // Below K = 256 the update's per-tile epilogue dominates and the CUDA-core
+    // kernel is faster (D = 18.6M, n = 32: 2.2 vs 0.9 TB/s at K = 32, even at
+    // K = 192); the projection is faster on the tensor cores at every m.
+    ws.tc_min_k = 256;
     trace("workspace %.3f GB at %p", ar.cap / 1e9, ar.base);
     if (cusolverDnCreate(&sol) != CUSOLVER_STATUS_SUCCESS) return fail(TRBL_ERR_CUDA, "cusolverDnCreate failed");
     TRBL_SOLVER(cusolverDnSetStream(sol, s));
+    if (cublasCreate(&blas) != CUBLAS_STATUS_SUCCESS) return fail(TRBL_ERR_CUDA, "cublasCreate failed");
+    if (cublasSetStream(blas, s) != CUBLAS_STATUS_SUCCESS) return fail(TRBL_ERR_CUDA, "cublasSetStream failed");
     TRBL_SOLVER(cusolverDnDsyevd_bufferSize(sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, mb, Aw, mb,
                                             theta, &lwork));
     trace("syevd lwork %d", lwork);
