@@ -296,9 +296,7 @@ int dot_launch(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, i
   const int mtiles = (m + MT - 1) / MT;
   const int target = 4 * ws.sm_count;
   int64_t nchunk = (target + mtiles - 1) / mtiles;
-  // at least kMinChunkRows rows per block: a small problem then leaves SMs
-  // free for the projections of other problems running beside it
-  const int64_t max_chunks = std::max<int64_t>(1, std::min<int64_t>((D + RS - 1) / RS, D / kMinChunkRows));
+  const int64_t max_chunks = (D + RS - 1) / RS;
   if (nchunk > max_chunks) nchunk = max_chunks;
   if (nchunk < 1) nchunk = 1;
   int64_t rows = (D + nchunk - 1) / nchunk;

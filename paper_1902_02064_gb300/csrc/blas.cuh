@@ -16,11 +16,6 @@ struct Workspace {
   int tc_min_k = 1;           // rowgemm_ws: smallest K sent to the tensor cores
 };
 
-// Smallest row chunk of a block of the solver's projections (block_dot):
-// problems of a few thousand rows take few SMs and leave the rest to
-// problems running beside them (batched solves).
-constexpr int64_t kMinChunkRows = 512;
-
 // Bytes of Workspace::partial needed by block_dot with these m, q.
 size_t block_dot_workspace_bytes(int m, int q, int sm_count);
 

@@ -133,7 +133,7 @@ int block_dot_tma(const float* B, int64_t ldb, int m, const float* W, int64_t ld
   const int64_t fit = int64_t(partial_bytes / per_chunk);
   if (fit < 1) return -1;
   int64_t nchunk = (4 * sm_count + mtiles - 1) / mtiles;
-  nchunk = std::max<int64_t>(1, std::min(std::min(nchunk, std::min((D + kRS - 1) / kRS, D / kMinChunkRows)), fit));
+  nchunk = std::max<int64_t>(1, std::min(std::min(nchunk, (D + kRS - 1) / kRS), fit));
   int64_t rows = (D + nchunk - 1) / nchunk;
   rows = (rows + kRS - 1) / kRS * kRS;
   nchunk = (D + rows - 1) / rows;

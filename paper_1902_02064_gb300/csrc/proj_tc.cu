@@ -494,7 +494,7 @@ int block_dot_tc(const float* B, int64_t ldb, int m, const float* W, int64_t ldw
   if (fit < 1) return -1;
   // one block per SM
   int64_t nchunk = std::max(1, sm_count / mtiles);
-  nchunk = std::max<int64_t>(1, std::min(std::min(nchunk, std::min((D + 31) / 32, D / kMinChunkRows)), fit));
+  nchunk = std::max<int64_t>(1, std::min(std::min(nchunk, (D + 31) / 32), fit));
   int64_t rows = (D + nchunk - 1) / nchunk;
   rows = (rows + 31) / 32 * 32;
   nchunk = (D + rows - 1) / rows;

@@ -447,18 +447,22 @@ struct Solver {
 
   // Out[rows x n] (row-major, ld ldo) = In[rows x K] (row-major, ld ldi) U,
   // U FP64 K x n row-major (ld n): the dense GEMMs of the restart and of the
-  // Ritz vectors, as cuBLAS GEMMs.  FP64 data in FP64; FP32 data with cuBLAS's
-  // FP32-accurate tensor-core emulation (operands split into three BF16
-  // parts) where the library offers it, plain FP32 otherwise.
+  // Ritz vectors.  Large FP32 ones (over 2e10 flops) run as cuBLAS GEMMs with
+  // the library's FP32-accurate tensor-core emulation (operands split into
+  // three BF16 parts) where it is offered, plain FP32 otherwise; FP64 data and
+  // small products use rowgemm (cuBLAS's set-up costs more than it saves
+  // there, and FP64 GEMMs run at the same FP64 rate either way).
   int gemm_rm(const T* In, int64_t ldi, int K, const double* U, int n, T* Out, int64_t ldo, int64_t rows) {
     if (rows <= 0 || n <= 0 || K <= 0) return TRBL_OK;
-    if (rows > INT32_MAX || ldi > INT32_MAX || ldo > INT32_MAX) return fail(TRBL_ERR_ARG, "GEMM too large");
+    const double flops = 2.0 * double(rows) * K * n;
+    if (std::is_same<T, double>::value || flops < 2e10 || rows > INT32_MAX || ldi > INT32_MAX || ldo > INT32_MAX)
+      return rowgemm<T>(In, ldi, K, U, n, n, Out, ldo, rows, 1.0, 0.0, s);
+    if (!blas) {
+      if (cublasCreate(&blas) != CUBLAS_STATUS_SUCCESS) return fail(TRBL_ERR_CUDA, "cublasCreate failed");
+      if (cublasSetStream(blas, s) != CUBLAS_STATUS_SUCCESS) return fail(TRBL_ERR_CUDA, "cublasSetStream failed");
+    }
     cublasStatus_t st;
-    if constexpr (std::is_same<T, double>::value) {
-      const double one = 1.0, zero = 0.0;
-      st = cublasDgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, n, int(rows), K, &one, U, n, In, int(ldi), &zero, Out,
-                       int(ldo));
-    } else {
+    {
       TRY(copy_cols<double, float>(U, n, Uf, n, K, n, s));
       const float one = 1.f, zero = 0.f;
       st = CUBLAS_STATUS_NOT_SUPPORTED;
@@ -784,8 +788,6 @@ struct Solver {
     trace("workspace %.3f GB at %p", ar.cap / 1e9, ar.base);
     if (cusolverDnCreate(&sol) != CUSOLVER_STATUS_SUCCESS) return fail(TRBL_ERR_CUDA, "cusolverDnCreate failed");
     TRBL_SOLVER(cusolverDnSetStream(sol, s));
-    if (cublasCreate(&blas) != CUBLAS_STATUS_SUCCESS) return fail(TRBL_ERR_CUDA, "cublasCreate failed");
-    if (cublasSetStream(blas, s) != CUBLAS_STATUS_SUCCESS) return fail(TRBL_ERR_CUDA, "cublasSetStream failed");
     TRBL_SOLVER(cusolverDnDsyevd_bufferSize(sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, mb, Aw, mb,
                                             theta, &lwork));
     trace("syevd lwork %d", lwork);
