@@ -242,7 +242,7 @@ typedef struct trbl_params {
   int max_iter;        /* block iterations cap; 0 = 100000 */
   int check_every;     /* Rayleigh-Ritz convergence test every this many block steps (restarts always
                           test); 0 = adaptive: a test once the block steps since the previous test
-                          have taken at least as long as that test did */
+                          have taken three times as long as that test did */
   uint64_t seed;       /* start block: uniform(-1,1) from splitmix64(seed<<32 + i*q + j) */
   double normH;        /* ||H|| used by tol; 0 = estimated by the solver (largest |Ritz value|) */
   int projections;     /* TRBL_PROJ_TENSOR (0, default) or TRBL_PROJ_CUDA_CORE: how the FP32
@@ -277,9 +277,9 @@ int trbl_solve(const trbl_hamiltonian* h, const trbl_params* p, double* evals, d
 /* Batched form of trbl_solve for nset Hamiltonians built on one basis (for
  * example many parameter sets of one model space), all with the same
  * parameters p.  One persistent launch of the block product serves every
- * set; the rest of a block step runs on one stream per set, forked from and
- * joined back into a private stream, and that step is captured into a CUDA
- * graph per basis size and replayed.  Rayleigh-Ritz tests and restarts run
+ * set, and each other operation of a block step is one launch over all
+ * sets; the step is captured into a CUDA graph per basis size and replayed
+ * on a private stream.  Rayleigh-Ritz tests and restarts run
  * between replays on host worker threads (each set on its own stream), all
  * sets testing at the same steps.  stats: iterations = block steps, ms_total
  * = wall time of the whole call, ms_apply = wall time of the batched block

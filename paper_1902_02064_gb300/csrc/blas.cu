@@ -106,6 +106,67 @@ __global__ void __launch_bounds__(32 * (QP / 4)) block_dot_kernel(
   }
 }
 
+
+// block_dot_kernel for several problems of equal shapes: grid z = problem;
+// problem z reads B[z], W[z] and writes partial[z].
+template <typename T, int QP>
+__global__ void __launch_bounds__(32 * (QP / 4)) block_dot_batched_kernel(
+    const T* const* __restrict__ Bs_, int64_t ldb, int m, const T* const* __restrict__ Ws_, int64_t ldw, int q,
+    int64_t D, int64_t rows_per_chunk, double* const* __restrict__ partials) {
+  const T* __restrict__ B = Bs_[blockIdx.z];
+  const T* __restrict__ W = Ws_[blockIdx.z];
+  double* __restrict__ partial = partials[blockIdx.z];
+  constexpr int RS = DotCfg<T>::RS;
+  constexpr int NT = 32 * (QP / 4);
+  __shared__ __align__(16) T Bs[RS][MT];
+  __shared__ __align__(16) T Ws[RS][QP];
+  const int tid = threadIdx.x;
+  const int tm = tid & 31, tq = tid >> 5;
+  const int m0 = blockIdx.x * MT;
+  const int64_t r_begin = int64_t(blockIdx.y) * rows_per_chunk;
+  const int64_t r_end = min(D, r_begin + rows_per_chunk);
+  T acc[4][4];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += RS) {
+    for (int idx = tid; idx < RS * MT; idx += NT) {
+      const int rr = idx / MT, cc = idx - rr * MT;
+      const int64_t r = r0 + rr;
+      Bs[rr][cc] = (r < r_end && m0 + cc < m) ? B[r * ldb + m0 + cc] : T(0);
+    }
+    for (int idx = tid; idx < RS * QP; idx += NT) {
+      const int rr = idx / QP, cc = idx - rr * QP;
+      const int64_t r = r0 + rr;
+      Ws[rr][cc] = (r < r_end && cc < q) ? W[r * ldw + cc] : T(0);
+    }
+    __syncthreads();
+    T t[4][4];
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) t[i][j] = T(0);
+#pragma unroll 4
+    for (int rr = 0; rr < RS; ++rr) {
+      T b[4], w[4];
+      lds4(&Bs[rr][4 * tm], b);
+      lds4(&Ws[rr][4 * tq], w);
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) t[i][j] = fma(b[i], w[j], t[i][j]);
+    }
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) acc[i][j] += t[i][j];
+    __syncthreads();
+  }
+  double* P = partial + int64_t(blockIdx.y) * m * q;
+  for (int i = 0; i < 4; ++i) {
+    const int bi = m0 + 4 * tm + i;
+    if (bi >= m) continue;
+    for (int j = 0; j < 4; ++j) {
+      const int wj = 4 * tq + j;
+      if (wj < q) P[int64_t(bi) * q + wj] = double(acc[i][j]);
+    }
+  }
+}
+
+
 __global__ void reduce_partials_kernel(const double* __restrict__ partial, int nchunk, int mq,
                                        double* __restrict__ C) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -113,6 +174,16 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partial, int n
   double s = 0.0;
   for (int c = 0; c < nchunk; ++c) s += partial[int64_t(c) * mq + i];
   C[i] = s;
+}
+
+__global__ void reduce_partials_batched_kernel(double* const* __restrict__ partial, int nchunk, int mq,
+                                               double* const* __restrict__ C) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= mq) return;
+  const double* P = partial[blockIdx.y];
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += P[int64_t(c) * mq + i];
+  C[blockIdx.y][i] = s;
 }
 
 // Out[r, c] = alpha * sum_k In[r, k] U[k, c] + beta * Out[r, c]
@@ -166,6 +237,63 @@ __global__ void __launch_bounds__(RT * CT / 16) rowgemm_kernel(
     }
   }
 }
+
+
+// rowgemm_kernel for several problems of equal shapes: grid z = problem;
+// problem z reads In[z], U[z] and updates Out[z].
+template <typename T, int RT, int CT>
+__global__ void __launch_bounds__(RT * CT / 16) rowgemm_batched_kernel(
+    const T* const* __restrict__ Ins, int64_t ldi, int K, const double* const* __restrict__ Us_, int64_t ldu, int n,
+    T* const* __restrict__ Outs, int64_t ldo, int64_t D, double alpha, double beta) {
+  const T* __restrict__ In = Ins[blockIdx.z];
+  const double* __restrict__ U = Us_[blockIdx.z];
+  T* __restrict__ Out = Outs[blockIdx.z];
+  constexpr int KC = 32;
+  constexpr int NT = RT * CT / 16;
+  constexpr int TR = RT / 4;
+  __shared__ __align__(16) T Bs[KC][RT + 4];
+  __shared__ __align__(16) T Us[KC][CT];
+  const int tid = threadIdx.x;
+  const int tr = tid % TR, tc = tid / TR;
+  const int64_t r0 = int64_t(blockIdx.x) * RT;
+  const int c0 = blockIdx.y * CT;
+  T acc[4][4];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    for (int idx = tid; idx < RT * KC; idx += NT) {
+      const int rr = idx / KC, kk = idx - rr * KC;
+      const int64_t r = r0 + rr;
+      Bs[kk][rr] = (r < D && k0 + kk < K) ? In[r * ldi + k0 + kk] : T(0);
+    }
+    for (int idx = tid; idx < KC * CT; idx += NT) {
+      const int kk = idx / CT, cc = idx - kk * CT;
+      Us[kk][cc] = (k0 + kk < K && c0 + cc < n) ? T(U[int64_t(k0 + kk) * ldu + c0 + cc]) : T(0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KC; ++kk) {
+      T b[4], u[4];
+      lds4(&Bs[kk][4 * tr], b);
+      lds4(&Us[kk][4 * tc], u);
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(b[i], u[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  for (int i = 0; i < 4; ++i) {
+    const int64_t r = r0 + 4 * tr + i;
+    if (r >= D) continue;
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + 4 * tc + j;
+      if (c >= n) continue;
+      T* o = Out + r * ldo + c;
+      const T v = T(alpha) * acc[i][j];
+      *o = (beta == 0.0) ? v : fma(T(beta), *o, v);
+    }
+  }
+}
+
 
 // Tall-skinny Out[:, 0:n] = alpha * In[:, 0:K] U + beta * Out with n <= NP <= 64:
 // U (K x n, FP64) is converted once per thread block into shared memory;
@@ -341,6 +469,70 @@ int dot_launch_capped(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, i
 void reduce_partials(const double* partial, int nchunk, int mq, double* C, cudaStream_t s) {
   reduce_partials_kernel<<<(mq + 255) / 256, 256, 0, s>>>(partial, nchunk, mq, C); note_launch();
 }
+
+template <typename T>
+int block_dot_batched(const T* const* B, int64_t ldb, int m, const T* const* W, int64_t ldw, int q, int64_t D,
+                      double* const* C, double* const* partial, size_t partial_bytes, int nset, cudaStream_t s) {
+  if (m <= 0 || nset <= 0 || D <= 0) return TRBL_OK;
+  constexpr int RS = DotCfg<T>::RS;
+  const int mtiles = (m + MT - 1) / MT;
+  const int64_t fit = int64_t(partial_bytes / (size_t(m) * q * sizeof(double)));
+  if (fit < 1) return fail(TRBL_ERR_ARG, "batched block_dot: workspace too small");
+  // about 1,024 rows per block: the problems together fill the GPU
+  int64_t nchunk = std::min<int64_t>(std::min<int64_t>((D + 1023) / 1024, fit), 65535);
+  nchunk = std::max<int64_t>(nchunk, 1);
+  int64_t rows = (D + nchunk - 1) / nchunk;
+  rows = (rows + RS - 1) / RS * RS;
+  nchunk = (D + rows - 1) / rows;
+  const dim3 grid{unsigned(mtiles), unsigned(nchunk), unsigned(nset)};
+#define TRBL_BDOT(QP) \
+  block_dot_batched_kernel<T, QP><<<grid, 32 * (QP / 4), 0, s>>>(B, ldb, m, W, ldw, q, D, rows, partial)
+  if (q <= 4) TRBL_BDOT(4);
+  else if (q <= 8) TRBL_BDOT(8);
+  else if (q <= 16) TRBL_BDOT(16);
+  else if (q <= 32) TRBL_BDOT(32);
+  else if (q <= 64) TRBL_BDOT(64);
+  else return fail(TRBL_ERR_ARG, "batched block_dot: q=%d > 64", q);
+#undef TRBL_BDOT
+  note_launch();
+  TRBL_CUDA(cudaGetLastError());
+  const int mq = m * q;
+  const dim3 rgrid{unsigned((mq + 255) / 256), unsigned(nset), 1u};
+  reduce_partials_batched_kernel<<<rgrid, 256, 0, s>>>(partial, int(nchunk), mq, C); note_launch();
+  TRBL_CUDA(cudaGetLastError());
+  return TRBL_OK;
+}
+
+template <typename T>
+int rowgemm_batched(const T* const* In, int64_t ldi, int K, const double* const* U, int64_t ldu, int n,
+                    T* const* Out, int64_t ldo, int64_t D, double alpha, double beta, int nset, cudaStream_t s) {
+  if (n <= 0 || D <= 0 || K <= 0 || nset <= 0) return TRBL_OK;
+  if (n <= 16) {
+    constexpr int RT = 128, CT = 16;
+    const dim3 grid{unsigned((D + RT - 1) / RT), unsigned((n + CT - 1) / CT), unsigned(nset)};
+    rowgemm_batched_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta);
+  } else if (n <= 32) {
+    constexpr int RT = 128, CT = 32;
+    const dim3 grid{unsigned((D + RT - 1) / RT), unsigned((n + CT - 1) / CT), unsigned(nset)};
+    rowgemm_batched_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta);
+  } else {
+    constexpr int RT = 64, CT = 64;
+    const dim3 grid{unsigned((D + RT - 1) / RT), unsigned((n + CT - 1) / CT), unsigned(nset)};
+    rowgemm_batched_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta);
+  }
+  note_launch();
+  TRBL_CUDA(cudaGetLastError());
+  return TRBL_OK;
+}
+
+template int block_dot_batched<float>(const float* const*, int64_t, int, const float* const*, int64_t, int, int64_t,
+                                      double* const*, double* const*, size_t, int, cudaStream_t);
+template int block_dot_batched<double>(const double* const*, int64_t, int, const double* const*, int64_t, int,
+                                       int64_t, double* const*, double* const*, size_t, int, cudaStream_t);
+template int rowgemm_batched<float>(const float* const*, int64_t, int, const double* const*, int64_t, int,
+                                    float* const*, int64_t, int64_t, double, double, int, cudaStream_t);
+template int rowgemm_batched<double>(const double* const*, int64_t, int, const double* const*, int64_t, int,
+                                     double* const*, int64_t, int64_t, double, double, int, cudaStream_t);
 
 template <typename T>
 int block_dot_capped(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, int64_t D, double* C,

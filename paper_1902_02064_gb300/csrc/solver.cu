@@ -120,6 +120,7 @@ __global__ void chol_kernel(const double* __restrict__ G, int q, double thresh_a
   }
 }
 
+
 // beta = R2 R1 (both upper triangular, q x q row-major)
 __global__ void upper_mul_kernel(const double* __restrict__ R2, const double* __restrict__ R1, int q,
                                  double* __restrict__ out) {
@@ -219,6 +220,142 @@ constexpr int kF2 = 80;    // pass-2 Cholesky
 constexpr int kInfo = 160; // syevd info
 constexpr int kTmaErr = 170;  // TMA wait timeout word
 constexpr int kFlagInts = 192;
+constexpr double kCheckRatio = 3.0;  // adaptive Rayleigh-Ritz cadence (see Solver::step)
+
+// ---- batched forms of a block step's small kernels ----
+// Per-set device pointers of the batched solver's step (entry s = set s).
+template <typename T>
+struct SetPtrs {
+  T* basis;
+  T* Vk;
+  double* C;
+  double* G;
+  double* R1;
+  double* R1i;
+  double* R2;
+  double* R2i;
+  double* beta;
+  double* Tm;
+  int* flags;
+  double thr1;  // absolute pivot threshold of the pass-1 Cholesky (tau ||H||)
+};
+
+// block s = set s: the pass-1 (pass = 1) or pass-2 Cholesky of its Gram
+// matrix (chol_kernel's arithmetic on the set's buffers)
+template <typename T>
+__global__ void chol_batched_kernel(const SetPtrs<T>* __restrict__ sp, int q, int pass, double thresh_rel,
+                                    double thresh_max) {
+  const SetPtrs<T> p = sp[blockIdx.x];
+  const double* __restrict__ G = p.G;
+  double* __restrict__ R = pass == 1 ? p.R1 : p.R2;
+  double* __restrict__ Rinv = pass == 1 ? p.R1i : p.R2i;
+  int* __restrict__ flags = p.flags + (pass == 1 ? kF1 : kF2);
+  const double thresh_abs = pass == 1 ? p.thr1 : 0.0;
+
+  __shared__ double Rs[64][65];
+  __shared__ double diag0[64];
+  __shared__ double dmax;
+  const int t = threadIdx.x;
+  for (int i = t; i < q * q; i += blockDim.x) {
+    const int r = i / q, c = i - r * q;
+    Rs[r][c] = (c >= r) ? G[i] : 0.0;
+  }
+  if (t < q) diag0[t] = G[t * q + t];
+  if (t == 0) flags[0] = 0;
+  if (t < q) flags[1 + t] = 0;
+  __syncthreads();
+  if (t == 0) {
+    double m = 0.0;
+    for (int j = 0; j < q; ++j) m = fmax(m, diag0[j]);
+    dmax = m;
+  }
+  __syncthreads();
+  for (int j = 0; j < q; ++j) {
+    if (t == 0) {
+      double d = Rs[j][j];
+      for (int k = 0; k < j; ++k) d -= Rs[k][j] * Rs[k][j];
+      const double lim = fmax(fmax(thresh_abs * thresh_abs, thresh_rel * thresh_rel * fmax(diag0[j], 0.0)),
+                              thresh_max * thresh_max * dmax);
+      if (!(d > lim)) {
+        flags[0] += 1;
+        flags[1 + j] = 1;
+        d = fmax(fabs(diag0[j]), 1e-300);
+      }
+      Rs[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    if (t > j && t < q) {
+      double s = Rs[j][t];
+      for (int k = 0; k < j; ++k) s -= Rs[k][j] * Rs[k][t];
+      Rs[j][t] = s / Rs[j][j];
+    }
+    __syncthreads();
+  }
+  for (int i = t; i < q * q; i += blockDim.x) {
+    const int r = i / q, c = i - r * q;
+    R[i] = (c >= r) ? Rs[r][c] : 0.0;
+  }
+  // column t of R^{-1} by back substitution
+  if (t < q) {
+    double x[64];
+    for (int j = t + 1; j < q; ++j) x[j] = 0.0;
+    for (int j = t; j >= 0; --j) {
+      double s = (j == t) ? 1.0 : 0.0;
+      for (int k = j + 1; k <= t; ++k) s -= Rs[j][k] * x[k];
+      x[j] = s / Rs[j][j];
+    }
+    for (int j = 0; j < q; ++j) Rinv[j * q + t] = (j <= t) ? x[j] : 0.0;
+  }
+}
+
+
+
+// grid (., sets): T_s[b0 + i][b0 + j] = (C_s[(b0+i) q + j] + C_s[(b0+j) q + i]) / 2
+template <typename T>
+__global__ void set_alpha_batched_kernel(const SetPtrs<T>* __restrict__ sp, int ldt, int b0, int q) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= q * q) return;
+  const SetPtrs<T> p = sp[blockIdx.y];
+  const int r = i / q, c = i - r * q;
+  p.Tm[int64_t(b0 + r) * ldt + b0 + c] = 0.5 * (p.C[(b0 + r) * q + c] + p.C[(b0 + c) * q + r]);
+}
+
+// grid (., sets): beta_s = R2_s R1_s, then its two copies in T_s
+template <typename T>
+__global__ void beta_batched_kernel(const SetPtrs<T>* __restrict__ sp, int ldt, int r0, int c0, int q, int set_t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= q * q) return;
+  const SetPtrs<T> p = sp[blockIdx.y];
+  const int r = i / q, c = i - r * q;
+  double s = 0.0;
+  for (int k = r; k <= c; ++k) s += p.R2[r * q + k] * p.R1[k * q + c];
+  const double v = (c >= r) ? s : 0.0;
+  p.beta[i] = v;
+  if (set_t) {
+    p.Tm[int64_t(r0 + r) * ldt + c0 + c] = v;
+    p.Tm[int64_t(c0 + c) * ldt + r0 + r] = v;
+  }
+}
+
+// grid (., sets): basis_s[:, col0 : col0 + q] = Vk_s
+template <typename T>
+__global__ void append_batched_kernel(const SetPtrs<T>* __restrict__ sp, int64_t D, int q, int ldb, int col0) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= D * q) return;
+  const SetPtrs<T> p = sp[blockIdx.y];
+  const int64_t r = i / q;
+  const int c = int(i - r * q);
+  p.basis[r * ldb + col0 + c] = p.Vk[i];
+}
+
+// out[2 s], out[2 s + 1] = the deficient-column counts of set s's two Cholesky passes
+template <typename T>
+__global__ void gather_counts_kernel(const SetPtrs<T>* __restrict__ sp, int nset, int* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nset) return;
+  out[2 * i] = sp[i].flags[kF1];
+  out[2 * i + 1] = sp[i].flags[kF2];
+}
 
 // Host-side progress trace, on when the environment sets TRBL_TRACE=1.
 static bool trace_on() {
@@ -538,8 +675,9 @@ struct Solver {
     ++iter;
     const bool need_restart = nb + q > mb;
     // Rayleigh-Ritz cadence: every check_every steps, or (check_every = 0)
-    // once the block steps since the previous test took as long as that test
-    const bool due = p->check_every > 0 ? iter % p->check_every == 0 : since_check_ms >= last_check_ms;
+    // once the block steps since the previous test took kCheckRatio times as
+    // long as that test (tests then cost at most 1 / (1 + kCheckRatio) of the time)
+    const bool due = p->check_every > 0 ? iter % p->check_every == 0 : since_check_ms >= kCheckRatio * last_check_ms;
     const bool check = need_restart || due || iter >= max_iter;
     have_ritz = false;
     if (check) {
@@ -858,13 +996,13 @@ namespace trbl {
 namespace {
 
 // Several Hamiltonians on one basis solved together.  One persistent launch
-// applies all of them (the grouped kernel over work items x sets); the rest
-// of a block step of every set runs on that set's own stream, forked from
-// and joined back into the driver's stream, and the whole step is captured
-// once per basis size into a CUDA graph and replayed.  Rayleigh-Ritz tests
-// and restarts run between replays on host worker threads, each set on its
-// own stream, so the small eigensolver calls of different sets overlap on
-// the GPU instead of running one after another.
+// applies all of them (the grouped kernel over work items x sets), and every
+// other operation of a block step (CGS2, alpha, Cholesky QR twice, beta, the
+// append) is one launch over all sets, reading the sets' pointers from
+// device arrays; the step is captured once per basis size into a CUDA graph
+// and replayed.  Rayleigh-Ritz tests and restarts run between replays on
+// host worker threads, each set on its own stream, so the small eigensolver
+// calls of different sets overlap on the GPU.
 template <typename T>
 struct BatchDriver {
   using clock = std::chrono::steady_clock;
@@ -872,15 +1010,30 @@ struct BatchDriver {
   trbl_params prm{};
   cudaStream_t s = nullptr;         // the driver's stream (capture origin)
   std::vector<cudaStream_t> ss;     // one stream per set
-  std::vector<cudaEvent_t> ev_join;  // end of a set's captured step
   std::vector<cudaEvent_t> ev_done;  // end of a set's host-driven work
-  cudaEvent_t ev_prod = nullptr;    // end of the batched product
   int nset = 0, nwork = 0, dtype = 0, device = 0, nthreads = 1;
   size_t smem = 0;
   int64_t D = 0;
   int q = 0, mb = 0;
   void* shared = nullptr;  // V_k and W of all sets, set-major
   void* tables = nullptr;  // DevH<T>[nset], DevG<T>[nset]
+  // batched step: device arrays of per-set pointers, per-set records, counts
+  void* bptr = nullptr;
+  T** P_basis = nullptr;
+  T** P_W = nullptr;
+  T** P_W2 = nullptr;
+  T** P_Vk = nullptr;
+  double** P_C1 = nullptr;
+  double** P_C2 = nullptr;
+  double** P_G = nullptr;
+  double** P_R1i = nullptr;
+  double** P_R2i = nullptr;
+  double** P_part = nullptr;
+  SetPtrs<T>* dsp = nullptr;
+  int* dcounts = nullptr;
+  SetPtrs<T>* hsp = nullptr;  // pinned: the records, thresholds refreshed before each step
+  int* hcounts = nullptr;     // pinned: 2 counts per set, then the three wait-timeout words
+  size_t part_bytes = 0;
   std::map<int, cudaGraphExec_t> graphs;
   std::vector<int> rc;
   std::vector<std::string> msg;
@@ -893,15 +1046,15 @@ struct BatchDriver {
       if (x) cudaStreamSynchronize(x);
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     for (auto* S : sets) delete S;
-    for (cudaEvent_t e : ev_join)
-      if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : ev_done)
       if (e) cudaEventDestroy(e);
-    if (ev_prod) cudaEventDestroy(ev_prod);
     for (cudaStream_t x : ss)
       if (x) cudaStreamDestroy(x);
     if (shared) cudaFree(shared);
     if (tables) cudaFree(tables);
+    if (bptr) cudaFree(bptr);
+    if (hsp) cudaFreeHost(hsp);
+    if (hcounts) cudaFreeHost(hcounts);
   }
 
   static double ms_since(clock::time_point t) {
@@ -976,14 +1129,11 @@ struct BatchDriver {
     rc.assign(nset, TRBL_OK);
     msg.assign(nset, std::string());
     ss.assign(nset, nullptr);
-    ev_join.assign(nset, nullptr);
     ev_done.assign(nset, nullptr);
     for (int i = 0; i < nset; ++i) {
       TRBL_CUDA(cudaStreamCreateWithFlags(&ss[i], cudaStreamNonBlocking));
-      TRBL_CUDA(cudaEventCreateWithFlags(&ev_join[i], cudaEventDisableTiming));
       TRBL_CUDA(cudaEventCreateWithFlags(&ev_done[i], cudaEventDisableTiming));
     }
-    TRBL_CUDA(cudaEventCreateWithFlags(&ev_prod, cudaEventDisableTiming));
     const size_t dq = size_t(D) * q;
     TRBL_CUDA(cudaMalloc(&shared, sizeof(T) * dq * 2 * nset));
     TRBL_CUDA(cudaMalloc(&tables, (sizeof(DevH<T>) + sizeof(DevG<T>)) * nset));
@@ -1012,24 +1162,94 @@ struct BatchDriver {
     for_sets(1, [&](int i) { return setup_set(hs[i], i); });
     for (int i = 0; i < nset; ++i)
       if (rc[i] != TRBL_OK) return fail(rc[i], "batched solve, set %d: %s", i, msg[i].c_str());
+    TRY(setup_pointers());
     trace("batch setup: %d sets, %.1f ms", nset, ms_since(t_start));
     return TRBL_OK;
   }
 
-  // Batched product on s, then each set's device step on its own stream,
-  // joined back into s.
+  // Device arrays of the sets' pointers for the batched step.
+  int setup_pointers() {
+    const size_t np = size_t(nset);
+    const size_t bytes = np * (4 * sizeof(T*) + 6 * sizeof(double*)) + np * sizeof(SetPtrs<T>) + 2 * np * sizeof(int) + 256;
+    TRBL_CUDA(cudaMalloc(&bptr, bytes));
+    TRBL_CUDA(cudaMallocHost(&hsp, np * sizeof(SetPtrs<T>)));
+    TRBL_CUDA(cudaMallocHost(&hcounts, (2 * np + 3) * sizeof(int)));
+    std::vector<char> host(bytes);
+    size_t off = 0;
+    auto place = [&](auto** dev, auto f) {
+      using P = std::remove_reference_t<decltype(**dev)>;
+      *dev = reinterpret_cast<P*>(static_cast<char*>(bptr) + off);
+      P* h = reinterpret_cast<P*>(host.data() + off);
+      for (int i = 0; i < nset; ++i) h[i] = f(*sets[i]);
+      off += np * sizeof(P);
+    };
+    place(&P_basis, [](Solver<T>& S) { return S.basis; });
+    place(&P_W, [](Solver<T>& S) { return S.W; });
+    place(&P_W2, [](Solver<T>& S) { return S.W2; });
+    place(&P_Vk, [](Solver<T>& S) { return S.Vk; });
+    place(&P_C1, [](Solver<T>& S) { return S.C; });
+    place(&P_C2, [&](Solver<T>& S) { return S.C + size_t(mb) * q; });
+    place(&P_G, [](Solver<T>& S) { return S.G; });
+    place(&P_R1i, [](Solver<T>& S) { return S.R1i; });
+    place(&P_R2i, [](Solver<T>& S) { return S.R2i; });
+    place(&P_part, [](Solver<T>& S) { return S.ws.partial; });
+    off = (off + 15) & ~size_t(15);
+    dsp = reinterpret_cast<SetPtrs<T>*>(static_cast<char*>(bptr) + off);
+    for (int i = 0; i < nset; ++i) {
+      Solver<T>& S = *sets[i];
+      hsp[i] = SetPtrs<T>{S.basis, S.Vk, S.C, S.G, S.R1, S.R1i, S.R2, S.R2i, S.beta, S.Tm, S.flags, 0.0};
+    }
+    off += np * sizeof(SetPtrs<T>);
+    dcounts = reinterpret_cast<int*>(static_cast<char*>(bptr) + off);
+    part_bytes = sets[0]->ws.partial_bytes;
+    TRBL_CUDA(cudaMemcpy(bptr, host.data(), bytes, cudaMemcpyHostToDevice));
+    return TRBL_OK;
+  }
+
+  // One block step of every set (Alg. 4 after the product): CGS2 against
+  // each basis, alpha into T, Cholesky QR twice, beta and the append of
+  // V_{k+1}, each a single launch over all sets; then the deficiency counts
+  // and wait-timeout words to pinned host memory.
   int enqueue(bool append) {
     T* V0 = static_cast<T*>(shared);
     const size_t dq = size_t(D) * q;
     TRY(launch_grouped_batch(tables, static_cast<char*>(tables) + sizeof(DevH<T>) * nset, nset, nwork, smem, V0, q,
                              int64_t(dq), V0 + dq * nset, q, int64_t(dq), q, dtype, s));
-    TRBL_CUDA(cudaEventRecord(ev_prod, s));
-    for (int i = 0; i < nset; ++i) {
-      TRBL_CUDA(cudaStreamWaitEvent(ss[i], ev_prod, 0));
-      TRY(sets[i]->step_device(append));
-      TRBL_CUDA(cudaEventRecord(ev_join[i], ss[i]));
-      TRBL_CUDA(cudaStreamWaitEvent(s, ev_join[i], 0));
+    const int nb = sets[0]->nb;
+    const T* const* cB = P_basis;
+    const T* const* cW = P_W;
+    const T* const* cW2 = P_W2;
+    TRY(block_dot_batched<T>(cB, mb, nb, cW, q, q, D, P_C1, P_part, part_bytes, nset, s));
+    TRY(rowgemm_batched<T>(cB, mb, nb, P_C1, q, q, P_W, q, D, -1.0, 1.0, nset, s));
+    TRY(block_dot_batched<T>(cB, mb, nb, cW, q, q, D, P_C2, P_part, part_bytes, nset, s));
+    TRY(rowgemm_batched<T>(cB, mb, nb, P_C2, q, q, P_W, q, D, -1.0, 1.0, nset, s));
+    const dim3 gq{unsigned((q * q + 127) / 128), unsigned(nset), 1u};
+    set_alpha_batched_kernel<T><<<gq, 128, 0, s>>>(dsp, mb, nb - q, q); note_launch();
+    TRY(block_dot_batched<T>(cW, q, q, cW, q, q, D, P_G, P_part, part_bytes, nset, s));
+    chol_batched_kernel<T><<<nset, 64, 0, s>>>(dsp, q, 1, 0.0, sets[0]->tau_max); note_launch();
+    TRY(rowgemm_batched<T>(cW, q, q, P_R1i, q, q, P_W2, q, D, 1.0, 0.0, nset, s));
+    TRY(block_dot_batched<T>(cW2, q, q, cW2, q, q, D, P_G, P_part, part_bytes, nset, s));
+    chol_batched_kernel<T><<<nset, 64, 0, s>>>(dsp, q, 2, 1e-3, 0.0); note_launch();
+    TRY(rowgemm_batched<T>(cW2, q, q, P_R2i, q, q, P_Vk, q, D, 1.0, 0.0, nset, s));
+    beta_batched_kernel<T><<<gq, 128, 0, s>>>(dsp, mb, nb, nb - q, q, append ? 1 : 0); note_launch();
+    if (append) {
+      const dim3 ga{unsigned((D * q + 255) / 256), unsigned(nset), 1u};
+      append_batched_kernel<T><<<ga, 256, 0, s>>>(dsp, D, q, mb, nb); note_launch();
     }
+    gather_counts_kernel<T><<<(nset + 127) / 128, 128, 0, s>>>(dsp, nset, dcounts); note_launch();
+    TRBL_CUDA(cudaGetLastError());
+    TRBL_CUDA(cudaMemcpyAsync(hcounts, dcounts, sizeof(int) * 2 * nset, cudaMemcpyDeviceToHost, s));
+    TRY(tma_error_to_host(hcounts + 2 * nset, s));
+    TRY(dot_error_to_host(hcounts + 2 * nset + 1, s));
+    TRY(tc_error_to_host(hcounts + 2 * nset + 2, s));
+    return TRBL_OK;
+  }
+
+  // Pivot thresholds of the sets' pass-1 Cholesky (tau ||H||, ||H|| being
+  // each set's current estimate) to the device records, before a step.
+  int refresh_thresholds() {
+    for (int i = 0; i < nset; ++i) hsp[i].thr1 = sets[i]->tau * sets[i]->normH;
+    TRBL_CUDA(cudaMemcpyAsync(dsp, hsp, sizeof(SetPtrs<T>) * nset, cudaMemcpyHostToDevice, s));
     return TRBL_OK;
   }
 
@@ -1070,6 +1290,7 @@ struct BatchDriver {
       const bool append = nb + q <= mb;
       const auto t0 = clock::now();
       for (int i = 0; i < nset; ++i) TRBL_CUDA(cudaStreamWaitEvent(s, ev_done[i], 0));
+      TRY(refresh_thresholds());
       if (it == 0) {
         TRY(enqueue(append));  // eager first step: lazily configured kernels set up outside capture
       } else {
@@ -1078,12 +1299,18 @@ struct BatchDriver {
         TRBL_CUDA(cudaGraphLaunch(ex, s));
       }
       TRBL_CUDA(cudaStreamSynchronize(s));
+      for (int i = 0; i < nset; ++i) {
+        int* hf = sets[i]->hflags;
+        hf[kF1] = hcounts[2 * i];
+        hf[kF2] = hcounts[2 * i + 1];
+        for (int k = 0; k < 3; ++k) hf[kTmaErr + k] = hcounts[2 * nset + k];
+      }
       const double t_step = ms_since(t0);
       ms_steps += t_step;
       since_check += t_step;
       // all sets test at the same steps: every check_every steps, or (adaptive)
-      // once the steps since the last test took as long as that test did
-      const bool due = prm.check_every > 0 ? (it + 1) % prm.check_every == 0 : since_check >= last_check;
+      // once the steps since the last test took kCheckRatio times as long as it
+      const bool due = prm.check_every > 0 ? (it + 1) % prm.check_every == 0 : since_check >= kCheckRatio * last_check;
       const bool check = due || !append;
       const auto t1 = clock::now();
       for_sets(0, [&](int i) {
