@@ -53,16 +53,19 @@ __device__ int two_body_sign_dev(uint32_t s, int a, int b, int c, int d) {
 __device__ __forceinline__ int bit_index(uint32_t x) { return __ffs(x) - 1; }
 
 // Adds dot to the bins of every like-particle term linking source s to target t.
-__device__ void add_like_terms(uint32_t t, uint32_t s, int n, double dot, double* b1, double* b2) {
+// The diagonal terms (s = t: n_a and n_a n_b) go to the thread block's
+// shared bins d1[a], d2[a n + b], which every row of the block hits.
+__device__ void add_like_terms(uint32_t t, uint32_t s, int n, double dot, double* b1, double* b2, double* d1,
+                               double* d2) {
   const uint32_t diff = t ^ s;
   const int moved = __popc(diff) >> 1;
   if (moved == 0) {
     for (uint32_t r = s; r; r &= r - 1) {
       const int a = bit_index(r);
-      atomicAdd(b1 + a * n + a, dot);
+      atomicAdd(d1 + a, dot);
       for (uint32_t r2 = r & (r - 1); r2; r2 &= r2 - 1) {
         const int b = bit_index(r2);
-        atomicAdd(b2 + ((size_t(a) * n + b) * n + a) * n + b, dot);  // n_a n_b, sign +1
+        atomicAdd(d2 + a * n + b, dot);  // n_a n_b, sign +1
       }
     }
   } else if (moved == 1) {
@@ -95,11 +98,8 @@ __device__ __forceinline__ double warp_dot(T x, T y) {
 
 // One warp per output row; lane k holds x_k[row] (nvec <= 32).
 template <typename T>
-__global__ void __launch_bounds__(256) grad_kernel(DevH<T> h, GradTables g, const T* __restrict__ X, int64_t ldx,
-                                                   int nvec, int64_t D) {
-  const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (r >= D) return;
+__device__ void grad_row(const DevH<T>& h, const GradTables& g, const T* __restrict__ X, int64_t ldx, int nvec,
+                         int64_t r, int lane, double* sAB, double* s1A, double* s2A, double* s1B, double* s2B) {
   int lo = 0, hi = h.nblk - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -136,7 +136,11 @@ __global__ void __launch_bounds__(256) grad_kernel(DevH<T> h, GradTables g, cons
         const double d = warp_dot(xr, xs);
         if (lane == 0) {
           const double v = ((ja.y ^ jb.y) & 1) ? -d : d;
-          atomicAdd(g.bAB + int64_t(ja.y >> 1) * nB2 + (jb.y >> 1), v);
+          const int ia = ja.y >> 1, ib = jb.y >> 1;
+          if (ia % (nA + 1) == 0 && ib % (nB + 1) == 0)
+            atomicAdd(sAB + (ia / (nA + 1)) * nB + ib / (nB + 1), v);  // n_a n_b: every row hits it
+          else
+            atomicAdd(g.bAB + int64_t(ia) * nB2 + ib, v);
         }
       }
     }
@@ -149,7 +153,7 @@ __global__ void __launch_bounds__(256) grad_kernel(DevH<T> h, GradTables g, cons
     const int64_t src = off + int64_t(sA) * nb + iB;
     const T xs = lane < nvec ? X[src * ldx + lane] : T(0);
     const double d = warp_dot(xr, xs);
-    if (lane == 0) add_like_terms(tA, g.bitsA[gA0 + sA], h.nA, d, g.b1A, g.b2A);
+    if (lane == 0) add_like_terms(tA, g.bitsA[gA0 + sA], h.nA, d, g.b1A, g.b2A, s1A, s2A);
   }
   // like-particle pairs of species B (proton unchanged)
   const uint32_t tB = g.bitsB[pB];
@@ -158,8 +162,44 @@ __global__ void __launch_bounds__(256) grad_kernel(DevH<T> h, GradTables g, cons
     const int64_t src = off + int64_t(iA) * nb + sB;
     const T xs = lane < nvec ? X[src * ldx + lane] : T(0);
     const double d = warp_dot(xr, xs);
-    if (lane == 0) add_like_terms(tB, g.bitsB[gB0 + sB], h.nB, d, g.b1B, g.b2B);
+    if (lane == 0) add_like_terms(tB, g.bitsB[gB0 + sB], h.nB, d, g.b1B, g.b2B, s1B, s2B);
   }
+}
+
+// Persistent blocks of 8 warps, a warp per row at a time.  The diagonal
+// bins (n_a n_b across species, n_a and n_a n_b within one), which every
+// row adds to, are summed in shared memory and added to the global bins
+// once per block; the other bins take global atomic adds.
+template <typename T>
+__global__ void __launch_bounds__(256) grad_kernel(DevH<T> h, GradTables g, const T* __restrict__ X, int64_t ldx,
+                                                   int nvec, int64_t D) {
+  __shared__ double sAB[32 * 32], s2A[32 * 32], s2B[32 * 32], s1A[32], s1B[32];
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int i = tid; i < 32 * 32; i += blockDim.x) sAB[i] = s2A[i] = s2B[i] = 0.0;
+  if (tid < 32) s1A[tid] = s1B[tid] = 0.0;
+  __syncthreads();
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t r = int64_t(blockIdx.x) * wpb + (tid >> 5); r < D; r += int64_t(gridDim.x) * wpb)
+    grad_row<T>(h, g, X, ldx, nvec, r, lane, sAB, s1A, s2A, s1B, s2B);
+  __syncthreads();
+  const int nA = h.nA, nB = h.nB;
+  for (int i = tid; i < nA * nB; i += blockDim.x) {
+    const int a = i / nB, b = i - a * nB;
+    const double v = sAB[a * nB + b];
+    if (v != 0.0) atomicAdd(g.bAB + int64_t(a * nA + a) * nB * nB + b * nB + b, v);
+  }
+  for (int i = tid; i < nA * nA; i += blockDim.x) {
+    const int a = i / nA, b = i - a * nA;
+    const double v = s2A[i];
+    if (v != 0.0) atomicAdd(g.b2A + ((size_t(a) * nA + b) * nA + a) * nA + b, v);
+  }
+  for (int i = tid; i < nB * nB; i += blockDim.x) {
+    const int a = i / nB, b = i - a * nB;
+    const double v = s2B[i];
+    if (v != 0.0) atomicAdd(g.b2B + ((size_t(a) * nB + b) * nB + a) * nB + b, v);
+  }
+  if (tid < nA && s1A[tid] != 0.0) atomicAdd(g.b1A + tid * nA + tid, s1A[tid]);
+  if (tid < nB && s1B[tid] != 0.0) atomicAdd(g.b1B + tid * nB + tid, s1B[tid]);
 }
 
 // Structural like-particle pairs (same 2M group, at most two particles moved)
@@ -299,7 +339,13 @@ extern "C" int trbl_grad(const trbl_hamiltonian* hc, const void* X, int64_t ldx,
   GradState* st = static_cast<GradState*>(h->grad);
   TRBL_CUDA(cudaMemsetAsync(st->g.b1A, 0, st->nbins * 8, s));
   const int64_t D = b->D;
-  const unsigned grid = unsigned((D * 32 + 255) / 256);
+  static const int sms = [] {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 148;
+  }();
+  const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>((D + 7) / 8, int64_t(4) * sms)));
   if (dtype == TRBL_F64)
     grad_kernel<double><<<grid, 256, 0, s>>>(h->d64, st->g, static_cast<const double*>(X), ldx, nvec, D);
   else
