@@ -280,6 +280,23 @@ def run_reference(args, rank, world):
 # our arm
 # ----------------------------------------------------------------------------
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest x over all ranks (a replicas job takes as long as its
+    slowest replica); x itself on a single process."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, seconds, world):
+    """Whole-job rate of `world` replicas that each processed
+    units_per_rank units, the job taking `seconds` (the slowest rank)."""
+    return world * units_per_rank / seconds
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_1902_02064_gb300 as trbl
@@ -333,13 +350,9 @@ def run_ours(args, rank, world):
     clk = clocks.stop()
     launches = trbl.trbl_kernel_launches() - l0
     st1 = sv.stats()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     ms_step = ms / args.steps
-    value = world * nnz * q * args.steps / (ms * 1e-3) / 1e9
+    value = job_throughput(nnz * q * args.steps, ms * 1e-3, world) / 1e9
     ms_apply = (st1["ms_apply"] - st0["ms_apply"]) / args.steps
     achieved = b_slab / (ms_apply * 1e-3) / 1e9
     traffic, _ = ncu_traffic(tune_rows)
@@ -357,12 +370,8 @@ def run_ours(args, rank, world):
         src, dst = (host_in, host_out) if k % 2 == 0 else (host_out, host_in)
         sv.step_host(src, dst)
     torch.cuda.synchronize()
-    el = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([el], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
-    e2e_value = world * nnz * q * args.steps / el / 1e9
+    el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e_value = job_throughput(nnz * q * args.steps, el, world) / 1e9
 
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
