@@ -392,7 +392,7 @@ def run_ours(args, rank, world):
                                for k in ("ms_apply", "ms_orth", "ms_qr", "ms_ritz", "ms_restart")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "apply_grouped_kernel<float, 4, 2>",
+                     "kernel": "apply_grouped_kernel<float, 8, 1>",
                      "algorithmic_bytes_per_launch": b_slab,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"},
         "clocks": clk,
