@@ -323,7 +323,7 @@ def run_ours(args, rank, world):
     b_slab = 4 * q * (R + D)  # bytes per apply, FP32
 
     stream = torch.cuda.current_stream()
-    # launch shape of the product: the autotuner times 32, 64, 128 and 256
+    # launch shape of the product: the autotuner times 16, 32, 64 and 128
     # neutron rows per work item and keeps the fastest (results do not change)
     tune_ms, tune_rows = trbl.apply_autotune(th, q, trbl.TRBL_F32)
     torch.cuda.empty_cache()
@@ -387,7 +387,7 @@ def run_ours(args, rank, world):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "apply": {"ms_per_launch": ms_apply, "gnzq_per_s": nnz * q / (ms_apply * 1e-3) / 1e9,
                   "share_of_step": ms_apply / ms_step,
-                  "autotune": {"rows_per_item": [32, 64, 128, 256], "ms": tune_ms, "chosen": tune_rows}},
+                  "autotune": {"rows_per_item": [16, 32, 64, 128], "ms": tune_ms, "chosen": tune_rows}},
         "phases_ms_per_step": {k: (st1[k] - st0[k]) / args.steps
                                for k in ("ms_apply", "ms_orth", "ms_qr", "ms_ritz", "ms_restart")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -612,7 +612,11 @@ def run_apply_only(args):
     R = slab_rows(bitsA, mA, mB, w.twoM)
     nnz = structural_nnz(bitsA, mA, bitsB, mB, blocks)
     dt = torch.float64 if args.fp64 else torch.float32
-    tune_ms, tune_rows = trbl.apply_autotune(th, q, trbl.TRBL_F64 if args.fp64 else trbl.TRBL_F32)
+    if args.rows:
+        tune_ms, tune_rows = None, args.rows
+        trbl.apply_set_rows(th, args.rows)
+    else:
+        tune_ms, tune_rows = trbl.apply_autotune(th, q, trbl.TRBL_F64 if args.fp64 else trbl.TRBL_F32)
     g = torch.Generator(device="cuda")
     g.manual_seed(w.seed)
     V = torch.rand((tb.dim, q), generator=g, device="cuda", dtype=dt) * 2 - 1
@@ -658,6 +662,8 @@ def main():
                     help="time only the block projection and update (FP32, both forms) at these sizes")
     ap.add_argument("--workload", default=WORKLOAD, help="workload of the solver steps (default: the 5+5 space)")
     ap.add_argument("--q", type=int, default=0)
+    ap.add_argument("--rows", type=int, default=0,
+                    help="--apply-only: fixed neutron rows per work item instead of the autotuner's choice")
     ap.add_argument("--fp64", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

@@ -295,11 +295,17 @@ int trbl_solve_batch(const trbl_hamiltonian* const* hs, int nset, const trbl_par
                      double* resid, void* evecs, int* status, trbl_stats* stats, void* stream);
 
 /* Times the block product of h at block size q and dtype for the candidate
- * work-item sizes 32, 64, 128 and 256 neutron rows and keeps the fastest;
+ * work-item sizes 16, 32, 64 and 128 neutron rows and keeps the fastest;
  * ms [4] (host, may be NULL) receives the average time per candidate and
  * *best_rows the choice.  Allocates two D x q scratch blocks for the timing.
  * Synchronises the stream. */
 int trbl_apply_autotune(trbl_hamiltonian* h, int q, int dtype, float* ms, int* best_rows, void* stream);
+
+/* Sets the block product's launch shape to rows_per_item neutron rows per
+ * work item (1..4096), as trbl_apply_autotune does with its choice; the
+ * product's results do not depend on it.  Host only; not while a product
+ * of h is running.  Errors: TRBL_ERR_ARG. */
+int trbl_apply_set_rows(trbl_hamiltonian* h, int rows_per_item);
 
 /* Stepwise form of trbl_solve for callers that drive the iteration
  * themselves.  A solver owns its device workspace (basis of D x max_basis

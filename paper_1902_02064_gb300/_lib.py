@@ -94,6 +94,7 @@ def lib():
         "trbl_solve_batch": (C.c_int, [C.POINTER(_VP), C.c_int, C.POINTER(trbl_params), _DP, _DP, _VP,
                                        C.POINTER(C.c_int), C.POINTER(trbl_stats), _VP]),
         "trbl_apply_autotune": (C.c_int, [_VP, C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int), _VP]),
+        "trbl_apply_set_rows": (C.c_int, [_VP, C.c_int]),
         "trbl_kernel_launches": (C.c_longlong, []),
         "trbl_last_error": (C.c_char_p, []),
     }
@@ -603,7 +604,7 @@ def solve_batch(hs, nev: int, q: int, max_basis: int, tol: float, precision: int
 
 
 def apply_autotune(h: "Hamiltonian", q: int, dtype: int = TRBL_F32, stream=None):
-    """Times the product for 32/64/128/256 neutron rows per work item and keeps
+    """Times the product for 16/32/64/128 neutron rows per work item and keeps
     the fastest; returns (times in ms, rows chosen)."""
     import torch
     ms = (C.c_float * 4)()
@@ -611,3 +612,8 @@ def apply_autotune(h: "Hamiltonian", q: int, dtype: int = TRBL_F32, stream=None)
     s = stream if stream is not None else torch.cuda.current_stream()
     _check(lib().trbl_apply_autotune(h.handle, int(q), int(dtype), ms, C.byref(best), s.cuda_stream))
     return list(ms), best.value
+
+
+def apply_set_rows(h: "Hamiltonian", rows_per_item: int):
+    """Sets the product's launch shape (neutron rows per work item)."""
+    _check(lib().trbl_apply_set_rows(h.handle, int(rows_per_item)))

@@ -10,7 +10,7 @@ using namespace trbl;
 
 extern "C" int trbl_apply_autotune(trbl_hamiltonian* h, int q, int dtype, float* ms, int* best_rows, void* stream) {
   clear_error();
-  static const int kCand[4] = {32, 64, 128, 256};
+  static const int kCand[4] = {16, 32, 64, 128};
   if (!h) return fail(TRBL_ERR_ARG, "null Hamiltonian");
   if (q < 1 || q > 64 || (dtype != TRBL_F32 && dtype != TRBL_F64)) return fail(TRBL_ERR_ARG, "bad q or dtype");
   if (!h->garena) return fail(TRBL_ERR_ARG, "the grouped product is not available for this basis");
@@ -51,4 +51,12 @@ extern "C" int trbl_apply_autotune(trbl_hamiltonian* h, int q, int dtype, float*
   if (rc) return rc;
   if (best_rows) *best_rows = bestr;
   return set_work_items(h, bestr);
+}
+
+extern "C" int trbl_apply_set_rows(trbl_hamiltonian* h, int rows_per_item) {
+  clear_error();
+  if (!h) return fail(TRBL_ERR_ARG, "null Hamiltonian");
+  if (rows_per_item < 1 || rows_per_item > 4096) return fail(TRBL_ERR_ARG, "rows per work item must be in [1, 4096]");
+  if (!h->garena) return fail(TRBL_ERR_ARG, "the grouped product is not available for this basis");
+  return set_work_items(h, rows_per_item);
 }

@@ -198,3 +198,20 @@ def test_grouped_and_row_kernels_agree(medium, dtype):
     bound = torch.from_numpy(abs(H) @ np.abs(Va.double().cpu().numpy())).cuda()
     diff = (Wa.double() - Wr[:, :q].double()).abs()
     assert torch.all(diff <= 2 * RTOL[dtype] * bound)
+
+
+def test_launch_shape_does_not_change_results(medium):
+    """trbl_apply_set_rows only regroups rows into thread blocks: every row's
+    summation order is the same, so W is bit-identical for any shape."""
+    w, B, H, tb, th = medium
+    V = torch.from_numpy(synth.random_block(B.dim, 32, 5)).float().cuda()
+    outs = []
+    for rows in (1, 7, 16, 128, 4096):
+        trbl.apply_set_rows(th, rows)
+        outs.append(th.apply(V).cpu())
+    trbl.apply_set_rows(th, 128)
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    _check(outs[0].double().numpy(), H, V.cpu().double().numpy(), torch.float32)
+    with pytest.raises(trbl.TrblError):
+        trbl.apply_set_rows(th, 0)

@@ -63,7 +63,7 @@ def test_apply_autotune_keeps_results():
     V = torch.from_numpy(synth.random_block(tb.dim, 8, 4)).float().cuda()
     W0 = h.apply(V).clone()
     ms, best = trbl.apply_autotune(h, 8, trbl.TRBL_F32)
-    assert best in (32, 64, 128, 256) and all(m > 0 for m in ms)
+    assert best in (16, 32, 64, 128) and all(m > 0 for m in ms)
     W1 = h.apply(V)
     torch.cuda.synchronize()
     assert torch.allclose(W0, W1, rtol=1e-6, atol=1e-6 * W0.abs().max().item())
