@@ -544,8 +544,8 @@ def gradient_batch(trbl, nset=64):
     t_solve_b = time.perf_counter() - t0
     euler = 0.0
     for k in range(nset):
-        for cl in trbl.clusters_of(ev[k], 1e-8 * st["normH"]):
-            g = trbl.hf_gradient(hs[k], X[k], cl)
+        cls = trbl.clusters_of(ev[k], 1e-8 * st["normH"])
+        for cl, g in zip(cls, trbl.hf_gradient_clusters(hs[k], X[k], cls)):
             euler = max(euler, abs(g @ inters[k].theta - ev[k][cl].sum()) / st["normH"])
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
@@ -553,8 +553,7 @@ def gradient_batch(trbl, nset=64):
     max_diff = 0.0
     for k in range(nset):
         e1, r1, X1, st1 = trbl.solve(hs[k], nev, q, mb, tol)
-        for cl in trbl.clusters_of(e1, 1e-8 * st1["normH"]):
-            trbl.hf_gradient(hs[k], X1, cl)
+        trbl.hf_gradient_clusters(hs[k], X1, trbl.clusters_of(e1, 1e-8 * st1["normH"]))
         max_diff = max(max_diff, float(np.abs(e1 - ev[k]).max()))
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0

@@ -170,6 +170,18 @@ int trbl_param_count(const trbl_basis* b, int64_t* n);
 int trbl_grad(const trbl_hamiltonian* h, const void* X, int64_t ldx, int nvec, int dtype, double* dtheta,
               int64_t nparams, void* stream);
 
+/* trbl_grad for several level clusters in one pass: the nvec columns of X
+ * are split into ncl clusters of consecutive columns, cluster c holding
+ * columns first[c] .. first[c+1] - 1 (host array, first[0] = 0, first[ncl]
+ * = nvec, increasing); dtheta[c * nparams + p] (host) receives the
+ * derivative of cluster c's eigenvalue sum, Tr(P_c dH/dtheta_p).  Same
+ * traversal of the product's elements as trbl_grad, each element's products
+ * summed per cluster; FP64 bins of ncl x (bins of trbl_grad) are kept with
+ * the Hamiltonian (grown as needed).  Synchronises the stream.  Errors:
+ * TRBL_ERR_ARG, TRBL_ERR_OOM, TRBL_ERR_CUDA. */
+int trbl_grad_clusters(const trbl_hamiltonian* h, const void* X, int64_t ldx, int nvec, int dtype,
+                       const int* first, int ncl, double* dtheta, int64_t nparams, void* stream);
+
 /* trbl_block_dot on the tensor cores (TRBL_PROJ_TENSOR arithmetic) for
  * FP32 data: same arguments, layout and errors, with dtype TRBL_F32 only,
  * q <= 32, B and W 16-byte aligned and ldb, ldw multiples of 4

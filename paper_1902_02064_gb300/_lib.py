@@ -91,6 +91,8 @@ def lib():
                                         C.c_int64, C.c_double, C.c_double, C.c_int, C.c_int, _VP]),
         "trbl_param_count": (C.c_int, [_VP, C.POINTER(C.c_int64)]),
         "trbl_grad": (C.c_int, [_VP, _VP, C.c_int64, C.c_int, C.c_int, _DP, C.c_int64, _VP]),
+        "trbl_grad_clusters": (C.c_int, [_VP, _VP, C.c_int64, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int, _DP,
+                                         C.c_int64, _VP]),
         "trbl_solve_batch": (C.c_int, [C.POINTER(_VP), C.c_int, C.POINTER(trbl_params), _DP, _DP, _VP,
                                        C.POINTER(C.c_int), C.POINTER(trbl_stats), _VP]),
         "trbl_apply_autotune": (C.c_int, [_VP, C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int), _VP]),
@@ -617,3 +619,38 @@ def apply_autotune(h: "Hamiltonian", q: int, dtype: int = TRBL_F32, stream=None)
 def apply_set_rows(h: "Hamiltonian", rows_per_item: int):
     """Sets the product's launch shape (neutron rows per work item)."""
     _check(lib().trbl_apply_set_rows(h.handle, int(rows_per_item)))
+
+
+def hf_gradient_clusters(h: "Hamiltonian", X, clusters, stream=None):
+    """Hellmann-Feynman gradients of several level clusters (lists of
+    consecutive column indices of X, as clusters_of returns) with one
+    trbl_grad_clusters pass per group of up to 32 columns; returns one
+    array per cluster (a cluster of more than 32 columns goes through
+    hf_gradient)."""
+    import torch
+    dt = TRBL_F64 if X.dtype == torch.float64 else TRBL_F32
+    n = trbl_param_count(h.basis.handle)
+    s = stream if stream is not None else torch.cuda.current_stream(X.device)
+    out = [None] * len(clusters)
+    k = 0
+    while k < len(clusters):
+        if len(clusters[k]) > 32:
+            out[k] = hf_gradient(h, X, clusters[k], stream)
+            k += 1
+            continue
+        group, cols = [], []
+        while k < len(clusters) and len(clusters[k]) <= 32 and len(cols) + len(clusters[k]) <= 32:
+            group.append(k)
+            cols.extend(clusters[k])
+            k += 1
+        sub = X[:, cols].contiguous()
+        first = [0]
+        for g in group:
+            first.append(first[-1] + len(clusters[g]))
+        fa = (C.c_int * len(first))(*first)
+        res = np.zeros((len(group), n))
+        _check(lib().trbl_grad_clusters(h.handle, sub.data_ptr(), sub.stride(0), sub.shape[1], dt, fa, len(group),
+                                        res.ctypes.data_as(_DP), n, s.cuda_stream))
+        for i, g in enumerate(group):
+            out[g] = res[i]
+    return out

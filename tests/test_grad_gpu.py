@@ -111,3 +111,45 @@ def test_grad_on_gradient_batch_space():
     g_or = og.hf_gradient(B, inter, x0)
     g_gpu = trbl.hf_gradient(th, X, [0])
     assert np.abs(g_gpu - g_or).max() <= 1e-10
+
+
+def test_grad_clusters_in_one_pass():
+    """trbl_grad_clusters: the gradients of all level clusters from one pass
+    equal those of one trbl_grad call per cluster (FP64: to 1e-12 of the
+    largest component; the atomic adds sum in a different order), each
+    satisfies the Euler identity, and the oracle agrees for the lowest
+    level.  Uneven clusters (1, 3 and 2 vectors) of the small space's exact
+    eigenvectors check the lane segmentation."""
+    sp = synth.make_space(synth.SPACE12_SHELLS)
+    inter = synth.draw_interaction(sp, sp, 100)
+    tb = trbl.Basis(sp, 4, sp, 4, 0)
+    th = trbl.Hamiltonian.from_interaction(tb, inter)
+    evals, resid, X, st = trbl.solve(th, 20, 8, 256, 1e-10)
+    normH = st["normH"]
+    cls = trbl.clusters_of(evals, 1e-8 * normH)
+    many = trbl.hf_gradient_clusters(th, X, cls)
+    for cl, g in zip(cls, many):
+        g1 = trbl.hf_gradient(th, X, cl)
+        assert np.abs(g - g1).max() <= 1e-12 * np.abs(g1).max()
+        assert abs(g @ inter.theta - evals[cl].sum()) <= 1e-9 * normH * len(cl)
+    odd = [[0], [1, 2, 3], [4, 5]]
+    for cl, g in zip(odd, trbl.hf_gradient_clusters(th, X, odd)):
+        g1 = trbl.hf_gradient(th, X, cl)
+        assert np.abs(g - g1).max() <= 1e-12 * np.abs(g1).max()
+    g32 = trbl.hf_gradient_clusters(th, X.float(), odd)
+    for cl, g in zip(odd, g32):
+        g1 = trbl.hf_gradient(th, X, cl)
+        assert np.abs(g - g1).max() <= 1e-5 * np.abs(g1).max()
+
+
+def test_grad_clusters_rejects_bad_boundaries(small):
+    w, sa, inter, B, ev, U, tb, th = small
+    X = torch.from_numpy(np.ascontiguousarray(U[:, :4])).cuda()
+    n = trbl.trbl_param_count(tb.handle)
+    out = np.zeros((2, n))
+    import ctypes
+    for first in ([0, 2, 2], [1, 2, 4], [0, 3, 5]):
+        fa = (ctypes.c_int * 3)(*first)
+        rc = trbl.lib().trbl_grad_clusters(th.handle, X.data_ptr(), 4, 4, trbl.TRBL_F64, fa, 2,
+                                           out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n, 0)
+        assert rc == trbl.TRBL_ERR_ARG
