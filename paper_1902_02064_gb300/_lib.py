@@ -539,7 +539,7 @@ def hf_gradient(h: "Hamiltonian", X, cols=None, stream=None) -> np.ndarray:
 
 class LowestEigenvalues:
     """torch.autograd.Function computing the nev lowest eigenvalues of H(theta)
-    with trbl_solve and their Hellmann-Feynman gradient with trbl_grad.
+    with trbl_solve and their Hellmann-Feynman gradient with trbl_grad_clusters.
 
     Within a cluster of levels closer than cluster_tol * ||H|| only the sum of
     the derivatives is defined; backward gives each member the cluster's mean
@@ -558,10 +558,9 @@ class LowestEigenvalues:
                 ev, rs, X, st = solve(h, nev, q, max_basis, tol, precision=precision, seed=seed)
                 cl = clusters_of(ev, cluster_tol * max(st["normH"], 1e-300))
                 G = np.zeros((nev, th.numel()))
-                for c in cl:
-                    g = hf_gradient(h, X, c) / len(c)
+                for c, g in zip(cl, hf_gradient_clusters(h, X, cl)):
                     for k in c:
-                        G[k] = g
+                        G[k] = g / len(c)
                 ctx.save_for_backward(torch.from_numpy(G).to(th.dtype))
                 return torch.from_numpy(ev).to(th.dtype)
 
