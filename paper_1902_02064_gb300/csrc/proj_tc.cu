@@ -7,10 +7,19 @@
 // Precision: every FP32 operand value x is split into TF32 parts
 // x = hi + lo (|x - hi - lo| <= 2^-22 |x|), and a product a b is formed as
 // a_hi b_hi + a_hi b_lo + a_lo b_hi (MMAs into FP32 accumulators in tensor
-// memory, summed when read out); the dropped a_lo b_lo is below 2^-22 |a b|.  The
-// projection drains its accumulator into FP64 registers every 64 stages
-// (2,048 rows), so FP32 sums never run over more than 2,048 rows; row
-// chunks are then combined in FP64 in a fixed order.
+// memory, summed when read out); the dropped a_lo b_lo is below 2^-22 |a b|.
+// The large a_hi b_hi products have an accumulator of their own, the two
+// small cross terms share a second one.
+//
+// The tensor cores' FP32 accumulation rounds toward zero, so every MMA into
+// a growing sum loses a fraction of an ulp in one direction: summed over
+// 2,048 rows (256 MMAs of K = 8, plus 256 of the cross terms into the same
+// accumulator) a Gram matrix came out about 1.6e-5 low on its diagonal,
+// leaving the block QR's vectors that much longer than unit length.  The
+// projection therefore drains its accumulators every kDrain = 4 stages (128
+// rows, 16 MMAs) into compensated FP32 sums (TwoSum, error-free for the
+// large part), which become FP64 per row chunk; row chunks are then
+// combined in FP64 in a fixed order.
 //
 // Warp-specialised pipeline of one thread block (320 threads), chained by
 // mbarriers only:
@@ -18,11 +27,13 @@
 //   (128-byte swizzle) into a ring of four raw stages;
 // * warps 2-9 (256 threads) convert a raw stage into split K-major operand
 //   tiles (a transpose for the projection, whose operands are row-major in
-//   K) in one of three conversion buffers, then release the raw stage;
+//   K) in one of three conversion buffers, then release the raw stage, and
+//   read a finished accumulator out one stage later, when its MMAs have
+//   had a stage's time to complete;
 // * warp 1 (one lane) issues the stage's MMAs and commits them to an
 //   mbarrier that frees the conversion buffer;
 // * two accumulators in tensor memory alternate between segments (the
-//   projection's 64-stage drains) or output tiles (the update), so the
+//   projection's 4-stage drains) or output tiles (the update), so the
 //   converter warps read one out while the MMAs fill the other.
 // Waits are bounded (tma.cuh): a timeout sets an error word the solver
 // reads at its next synchronisation, and the block waits (bounded) for its
@@ -47,7 +58,7 @@ namespace {
 constexpr int kConvWarps = 8;
 constexpr int kThreadsTC = 64 + 32 * kConvWarps;  // producer warp, MMA warp, converter warps
 constexpr int kRawStages = 4;
-constexpr int kDrain = 64;          // projection stages per accumulator segment
+constexpr int kDrain = 4;           // projection stages per accumulator segment
 constexpr int kTile = 128;          // MMA M: columns of B (projection) or rows of In (update)
 constexpr int kN = 32;              // MMA N (one accumulator = 32 tensor-memory columns)
 constexpr int kConvBufs = 3;
@@ -99,7 +110,8 @@ __device__ __forceinline__ void transpose_split(const unsigned char* box, unsign
 // Issues the split MMAs of the four K steps of a stage.  B's hi and lo
 // tiles are adjacent (rows 0-31 hi, 32-63 lo), so one N = 64 MMA forms
 // a_hi b_hi (accumulator columns 0-31) and a_hi b_lo (columns 32-63) with
-// one read of a_hi; a second, N = 32, adds a_lo b_hi into columns 0-31.
+// one read of a_hi; a second, N = 32, adds a_lo b_hi into columns 32-63,
+// beside the other small cross term.
 __device__ __forceinline__ void issue_split_mmas(uint32_t acc, const unsigned char* cv, bool first) {
   const uint64_t dah = sdesc_k128(cv), dal = sdesc_k128(cv + kTileBytes);
   const uint64_t db = sdesc_k128(cv + 2 * kTileBytes);
@@ -107,7 +119,7 @@ __device__ __forceinline__ void issue_split_mmas(uint32_t acc, const unsigned ch
   for (int kk = 0; kk < 4; ++kk) {
     const uint64_t o = uint64_t(2 * kk);  // +32 bytes in the start-address field
     mma_tf32(acc, dah + o, db + o, kIdesc2, (first && kk == 0) ? 0u : 1u);
-    mma_tf32(acc, dal + o, db + o, kIdesc, 1u);
+    mma_tf32(acc + uint32_t(kN), dal + o, db + o, kIdesc, 1u);
   }
 }
 
@@ -194,16 +206,31 @@ __device__ __forceinline__ void warp_arrive_async(uint64_t* bar, int lane) {
 }
 
 // This converter thread's 16 accumulator values (its lane's row, its warp's
-// column half): the sum of the a_hi b_hi + a_lo b_hi and a_hi b_lo columns of
-// accumulator a.  The warp index mod 4 selects the 32 tensor-memory lanes a
-// warp may read.
-__device__ __forceinline__ void acc_load(uint32_t tmem, int warp, int a, float (&v)[16]) {
+// column half) of accumulator a: the a_hi b_hi columns in v, the columns of
+// the two cross terms in w.  The warp index mod 4 selects the 32
+// tensor-memory lanes a warp may read.
+__device__ __forceinline__ void acc_load2(uint32_t tmem, int warp, int a, float (&v)[16], float (&w)[16]) {
   const uint32_t base = tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(a * 2 * kN + 16 * ((warp - 2) >> 2));
-  float w[16];
   tmem_ld16(base, v);
   tmem_ld16(base + kN, w);
+}
+
+// The same, summed.
+__device__ __forceinline__ void acc_load(uint32_t tmem, int warp, int a, float (&v)[16]) {
+  float w[16];
+  acc_load2(tmem, warp, a, v, w);
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] += w[i];
+}
+
+// s + e := hi + x exactly (Knuth's TwoSum, round-to-nearest adds that the
+// compiler may not contract or reorder).
+__device__ __forceinline__ void two_sum(float& hi, float x, float& e) {
+  const float s = __fadd_rn(hi, x);
+  const float xb = __fsub_rn(s, hi);
+  const float hb = __fsub_rn(s, xb);
+  e = __fadd_rn(__fsub_rn(hi, hb), __fsub_rn(x, xb));
+  hi = s;
 }
 
 }  // namespace
@@ -215,7 +242,9 @@ namespace {
 // rows are B's columns (M = 128), its columns W's (N = 32), K runs over the
 // chunk's rows.  Raw stage j: 4 boxes of B (32 rows x 32 columns) and one of
 // W; conversion transposes them into K-major split tiles in buffer j mod 3.
-// Accumulator segment g (stages 64 g .. 64 g + 63) uses accumulator g & 1.
+// Accumulator segment g (stages kDrain g .. kDrain g + kDrain - 1) uses
+// accumulator g & 1; the converters read segment g out after converting
+// the first stage of segment g + 1 (the last segment after the loop).
 __global__ void __launch_bounds__(kThreadsTC, 1)
     block_dot_tc_kernel(const __grid_constant__ CUtensorMap tb, const __grid_constant__ CUtensorMap tw, int m, int q,
                         int64_t D, int64_t rows_per_chunk, double* __restrict__ partial) {
@@ -233,9 +262,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   tc_setup(sh, warp);
   const uint32_t tmem = sh.tmem;
   int64_t issued = 0, committed = -1;
-  double acc[16];
+  float sum_hi[16], sum_lo[16];  // compensated sum of the drained segments
 #pragma unroll
-  for (int i = 0; i < 16; ++i) acc[i] = 0.0;
+  for (int i = 0; i < 16; ++i) sum_hi[i] = sum_lo[i] = 0.f;
 
   if (warp == 0) {
     // ---- TMA producer ----
@@ -277,8 +306,28 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     const int P = ct >> 3, a8 = ct & 7;
     const int rb = a8, cb = ((P & 1) << 2) + (((a8 >> 1) + ((P >> 1) & 3)) & 3);
     const int mybox = P >> 3;
+    // segment g's accumulator into the compensated sums
+    auto drain = [&](int64_t g) -> bool {
+      const int a = int(g & 1);
+      if (!wait_or_abort(sh, &sh.accfull[a], uint32_t((g >> 1) & 1))) return false;
+      tc_fence_after();
+      float v[16], w[16];
+      acc_load2(tmem, warp, a, v, w);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh.accfree[a]);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        float e;
+        two_sum(sum_hi[i], v[i], e);
+        sum_lo[i] = __fadd_rn(sum_lo[i], __fadd_rn(e, w[i]));
+      }
+      return true;
+    };
+    bool live = true;
     for (int64_t j = 0; j < njobs; ++j) {
       const int s = int(j % kRawStages), c = int(j % kConvBufs);
+      live = false;
       if (!wait_or_abort(sh, &sh.full[s], uint32_t((j / kRawStages) & 1))) break;
       if (j >= kConvBufs && !wait_or_abort(sh, &sh.mdone[c], uint32_t((j / kConvBufs - 1) & 1))) break;
       if (aborted(sh)) break;
@@ -291,21 +340,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&sh.empty[s]);
       warp_arrive_async(&sh.cfull[c], lane);
-      if (j % kDrain == kDrain - 1 || j == njobs - 1) {
-        // segment done: move its accumulator into FP64 registers
-        const int64_t g = j / kDrain;
-        const int a = int(g & 1);
-        if (!wait_or_abort(sh, &sh.accfull[a], uint32_t((g >> 1) & 1))) break;
-        tc_fence_after();
-        float v[16];
-        acc_load(tmem, warp, a, v);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) acc[i] += double(v[i]);
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&sh.accfree[a]);
-      }
+      if (j % kDrain == 0 && j > 0 && !drain(j / kDrain - 1)) break;
+      live = true;
     }
+    if (live && njobs > 0 && !aborted(sh)) drain((njobs - 1) / kDrain);
   }
   const bool ok = !aborted(sh);
   tc_finish(sh, warp, lane, issued, committed);
@@ -316,7 +354,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     if (i < m) {
 #pragma unroll
       for (int k = 0; k < 16; ++k)
-        if (c0 + k < q) Pp[int64_t(i) * q + c0 + k] = acc[k];
+        if (c0 + k < q) Pp[int64_t(i) * q + c0 + k] = double(sum_hi[k]) + double(sum_lo[k]);
     }
   }
 }
