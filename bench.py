@@ -666,6 +666,8 @@ def main():
     ap.add_argument("--no-ttn", action="store_true", help="skip the time-to-nev solves")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-set gradient batch")
     ap.add_argument("--no-proj", action="store_true", help="skip the projection kernels' own timing")
+    ap.add_argument("--arms", default=None, metavar="LABEL,...",
+                    help="with --ttn-large: run only these arms (fp64_q16, mixed_q16, fp64_q1, mixed_q32)")
     ap.add_argument("--ttn-large", metavar="WORKLOAD", default=None,
                     help="only: time to nev eigenpairs at 1e-6 ||H|| on a large workload (s20_4p4n: mixed, "
                          "FP64 block and FP64 q = 1 arms; s20_5p5n: mixed) and print one JSON line")
@@ -692,6 +694,11 @@ def main():
         else:
             arms = (("fp64_q%d" % w.q, trbl.TRBL_PREC_F64, w.q), ("mixed_q%d" % w.q, trbl.TRBL_PREC_MIXED, w.q),
                     ("fp64_q1", trbl.TRBL_PREC_F64, 1))
+        if args.arms:
+            keep = args.arms.split(",")
+            arms = tuple(a for a in arms if a[0] in keep)
+            if not arms:
+                sys.exit("--arms: none of %s among this workload's arms" % keep)
         print(json.dumps({"time_to_nev": time_to_nev_large(trbl, args.ttn_large, arms)}), flush=True)
     elif args.impl == "reference":
         run_reference(args, rank, world)
