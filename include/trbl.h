@@ -231,7 +231,9 @@ int trbl_block_dot_noalloc(const void* B, int64_t ldb, int m, const void* W, int
  * Out = alpha In U + beta Out (mixed precision).  TRBL_PROJ_TENSOR: tcgen05
  * tensor-core MMAs on split TF32 operands (x = hi + lo with TF32 hi and lo,
  * |x - hi - lo| <= 2^-22 |x|; a b formed as a_hi b_hi + a_hi b_lo + a_lo b_hi
- * in FP32; projections drain to FP64 every 2,048 rows), for q or n <= 32
+ * in FP32 tensor memory; projections drain every 128 rows into compensated
+ * FP32 sums, FP64 per row chunk, which keeps the tensor cores' round-toward-
+ * zero accumulation from biasing the sums), for q or n <= 32
  * and 16-byte aligned row-major operands, other shapes falling back to the
  * CUDA cores.  The solver sends updates with K < 256 to the CUDA cores,
  * which are faster there.  TRBL_PROJ_CUDA_CORE: FP32 FMAs on the CUDA cores with FP64

@@ -5,8 +5,9 @@ the update Out = alpha In U + beta Out (trbl_block_update; "W -= V C" and
 W R^-1), and the mixed-precision solver on both projection paths.
 
 Tolerance: each product a b is formed from TF32 parts with relative error
-below 2^-21, and FP32 sums run over at most 2,048 rows (projection) or the
-K columns (update) before FP64 takes over; for random data the realised
+below 2^-21, and tensor-core FP32 sums run over at most 128 rows
+(projection; compensated FP32, then FP64, beyond) or the K columns
+(update); for random data the realised
 error is far inside |err| <= 1e-5 * (|B|^T |W|) (resp. |In| |U| + |beta Out|),
 the bound the CUDA-core FP32 kernels are held to."""
 import json
