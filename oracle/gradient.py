@@ -16,7 +16,7 @@ listed, including those whose value is zero (off-diagonal one-body terms).
 """
 from __future__ import annotations
 
-from typing import Dict, Tuple
+from typing import Dict
 
 import numpy as np
 

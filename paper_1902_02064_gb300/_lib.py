@@ -3,8 +3,7 @@ small owning wrappers (Basis, Hamiltonian) and ``solve``."""
 from __future__ import annotations
 
 import ctypes as C
-import os
-from typing import Optional, Sequence
+from typing import Sequence
 
 import numpy as np
 

@@ -8,7 +8,6 @@ jumps.
 """
 import os
 
-import numpy as np
 import pytest
 
 import synth
