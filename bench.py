@@ -268,7 +268,9 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": times / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "q": w.q, "dim": 18600516},
+        "data": "synthetic", "config": {"workload": WORKLOAD, "dim": 18600516, "q": w.q, "nev": w.nev,
+                                        "max_basis": w.max_basis, "precision": "FP64 oracle, one row at a time",
+                                        "parallelism": "one host core"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "%d random rows of H.V per %d steps, FP64 oracle, one core" % (rows, args.steps)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
