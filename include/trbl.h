@@ -355,6 +355,33 @@ int trbl_solver_stats(trbl_solver* s, trbl_stats* stats);
 int trbl_solver_finish(trbl_solver* s, double* evals, double* resid, void* evecs, trbl_stats* stats);
 void trbl_solver_destroy(trbl_solver* s);
 
+/* Checkpoint and resume of a stepwise solver.  The state between block
+ * steps of Alg. 4 is the Lanczos basis V_1 .. V_k (after a thick restart:
+ * the kept Ritz vectors and the new block, Eq. (trb-tmat)), the current
+ * block V_{k+1}, the projected matrix T and a few counters; it is written
+ * to and read from caller-owned host memory in a library-defined format
+ * (a header, then T as max_basis x max_basis FP64, V_{k+1} as D x q and the
+ * basis as D x (stored vectors), row-major, in the precision's element
+ * type).  Checkpoints are meant for host memory or files of the same
+ * build; the paper stores its Lanczos vectors on disk only for want of
+ * memory (App. C), not to resume.
+ *
+ * trbl_solver_state_bytes: *bytes = size of the state now (it grows with
+ *   the basis; smallest right after a restart).
+ * trbl_solver_save: writes the state to host (at least state_bytes bytes;
+ *   pinned memory is faster).  Synchronises the solver's stream.  Errors:
+ *   TRBL_ERR_ARG (null, too small, or the solver has already converged:
+ *   finish it instead), TRBL_ERR_CUDA.
+ * trbl_solver_load: replaces the state of s, created with the same
+ *   Hamiltonian dimension, q, max_basis, keep and precision, by a saved
+ *   one; the next steps continue the saved iteration (with a fixed
+ *   check_every the results equal an uninterrupted run's).  Statistics
+ *   resume from the saved counts.  Errors: TRBL_ERR_ARG (not a state of
+ *   this library, or saved with other sizes), TRBL_ERR_CUDA. */
+int trbl_solver_state_bytes(trbl_solver* s, int64_t* bytes);
+int trbl_solver_save(trbl_solver* s, void* host, int64_t bytes);
+int trbl_solver_load(trbl_solver* s, const void* host, int64_t bytes);
+
 /* Number of kernels this library has launched in the process so far
  * (every entry point counts its own launches; library calls such as the
  * cuSOLVER eigensolver are not counted). */

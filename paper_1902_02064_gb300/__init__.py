@@ -19,7 +19,7 @@ from ._lib import (  # noqa: F401
     trbl_apply_block, trbl_solve, trbl_last_error, trbl_kernel_launches, trbl_block_dot, block_dot,
     trbl_block_dot_noalloc, trbl_block_dot_tc, trbl_block_update, block_update,
     trbl_solver_create, trbl_solver_step, trbl_solver_step_host, trbl_solver_block,
-    trbl_solver_stats, trbl_solver_destroy,
+    trbl_solver_stats, trbl_solver_destroy, trbl_solver_state_bytes, trbl_solver_save, trbl_solver_load,
     trbl_param_count, trbl_grad, arrays_from_theta, clusters_of, hf_gradient, hf_gradient_clusters, LowestEigenvalues,
     solve_batch, apply_autotune, apply_set_rows,
     Basis, Hamiltonian, Solver, solve,

@@ -82,6 +82,9 @@ def lib():
         "trbl_solver_stats": (C.c_int, [_VP, C.POINTER(trbl_stats)]),
         "trbl_solver_finish": (C.c_int, [_VP, _DP, _DP, _VP, C.POINTER(trbl_stats)]),
         "trbl_solver_destroy": (None, [_VP]),
+        "trbl_solver_state_bytes": (C.c_int, [_VP, C.POINTER(C.c_int64)]),
+        "trbl_solver_save": (C.c_int, [_VP, _VP, C.c_int64]),
+        "trbl_solver_load": (C.c_int, [_VP, _VP, C.c_int64]),
         "trbl_block_dot": (C.c_int, [_VP, C.c_int64, C.c_int, _VP, C.c_int64, C.c_int, C.c_int64, C.c_int, _VP, _VP]),
         "trbl_block_dot_noalloc": (C.c_int, [_VP, C.c_int64, C.c_int, _VP, C.c_int64, C.c_int, C.c_int64, C.c_int,
                                              _VP, _VP]),
@@ -390,6 +393,20 @@ def trbl_solver_destroy(sv: int):
     lib().trbl_solver_destroy(sv)
 
 
+def trbl_solver_state_bytes(sv: int) -> int:
+    n = C.c_int64()
+    _check(lib().trbl_solver_state_bytes(sv, C.byref(n)))
+    return n.value
+
+
+def trbl_solver_save(sv: int, host_ptr: int, nbytes: int):
+    _check(lib().trbl_solver_save(sv, host_ptr, nbytes))
+
+
+def trbl_solver_load(sv: int, host_ptr: int, nbytes: int):
+    _check(lib().trbl_solver_load(sv, host_ptr, nbytes))
+
+
 class Solver:
     """Stepwise thick-restart block Lanczos (trbl_solver_* entry points)."""
 
@@ -415,6 +432,17 @@ class Solver:
 
     def block(self):
         return trbl_solver_block(self.handle)
+
+    def save(self) -> np.ndarray:
+        """Checkpoint: the solver's state between steps as a host byte array."""
+        buf = np.empty(trbl_solver_state_bytes(self.handle), dtype=np.uint8)
+        trbl_solver_save(self.handle, buf.ctypes.data, buf.nbytes)
+        return buf
+
+    def load(self, state: np.ndarray):
+        """Resume from a checkpoint taken by save() (same sizes and precision)."""
+        state = np.ascontiguousarray(state, dtype=np.uint8)
+        trbl_solver_load(self.handle, state.ctypes.data, state.nbytes)
 
     def stats(self) -> dict:
         return trbl_solver_stats(self.handle)

@@ -28,6 +28,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <type_traits>
 #include <climits>
 #include <cmath>
@@ -808,6 +809,97 @@ struct Solver {
     st->ms_restart = ms_restart;
   }
 
+  // ---- checkpoint: the state between block steps ----
+  // Header, then T (mb x mb FP64), beta (q x q FP64, for the residual
+  // estimates of a finish right after a load), V_k (D x q) and the basis
+  // (D x nb, packed), all in host memory.
+  struct State {
+    uint64_t magic;
+    int32_t version, dtype, q, mb, ls, nb, iter, restarts, conv, pad;
+    int64_t D;
+    uint64_t reseed;
+    double normH, since_check_ms, last_check_ms, ms[5];
+  };
+  static constexpr uint64_t kStateMagic = 0x5441545342525454ull;
+  size_t state_bytes_for(int n) const {
+    return sizeof(State) + sizeof(double) * (size_t(mb) * mb + size_t(q) * q) + sizeof(T) * size_t(D) * (q + n);
+  }
+  size_t state_bytes() const { return state_bytes_for(nb); }
+
+  int save(void* host, int64_t bytes) {
+    if (done) return fail(TRBL_ERR_ARG, "the solver has converged: finish it instead of saving its state");
+    const size_t need = state_bytes();
+    if (!host || bytes < 0 || size_t(bytes) < need) return fail(TRBL_ERR_ARG, "the state needs %zu bytes", need);
+    State st{};
+    st.magic = kStateMagic;
+    st.version = 1;
+    st.dtype = dtype;
+    st.q = q;
+    st.mb = mb;
+    st.ls = ls;
+    st.nb = nb;
+    st.iter = iter;
+    st.restarts = restarts;
+    st.conv = conv;
+    st.D = D;
+    st.reseed = reseed;
+    st.normH = normH;
+    st.since_check_ms = since_check_ms;
+    st.last_check_ms = last_check_ms;
+    const double ms[5] = {ms_apply, ms_orth, ms_qr, ms_ritz, ms_restart};
+    std::memcpy(st.ms, ms, sizeof(ms));
+    unsigned char* o = static_cast<unsigned char*>(host);
+    std::memcpy(o, &st, sizeof(st));
+    o += sizeof(st);
+    TRBL_CUDA(cudaMemcpyAsync(o, Tm, sizeof(double) * mb * mb, cudaMemcpyDeviceToHost, s));
+    o += sizeof(double) * mb * mb;
+    TRBL_CUDA(cudaMemcpyAsync(o, beta, sizeof(double) * q * q, cudaMemcpyDeviceToHost, s));
+    o += sizeof(double) * q * q;
+    TRBL_CUDA(cudaMemcpyAsync(o, Vk, sizeof(T) * D * q, cudaMemcpyDeviceToHost, s));
+    o += sizeof(T) * D * q;
+    TRBL_CUDA(cudaMemcpy2DAsync(o, sizeof(T) * nb, basis, sizeof(T) * mb, sizeof(T) * nb, size_t(D),
+                                cudaMemcpyDeviceToHost, s));
+    TRBL_CUDA(cudaStreamSynchronize(s));
+    return TRBL_OK;
+  }
+
+  int load(const void* host, int64_t bytes) {
+    if (!host || bytes < int64_t(sizeof(State))) return fail(TRBL_ERR_ARG, "not a solver state");
+    State st;
+    std::memcpy(&st, host, sizeof(st));
+    if (st.magic != kStateMagic || st.version != 1) return fail(TRBL_ERR_ARG, "not a solver state of this library");
+    if (st.dtype != dtype || st.q != q || st.mb != mb || st.ls != ls || st.D != D)
+      return fail(TRBL_ERR_ARG, "state saved with other sizes (D %lld, q %d, max_basis %d, keep %d, precision)",
+                  (long long)st.D, st.q, st.mb, st.ls);
+    if (st.nb < q || st.nb > mb) return fail(TRBL_ERR_ARG, "corrupt state (basis size %d)", st.nb);
+    if (size_t(bytes) < state_bytes_for(st.nb)) return fail(TRBL_ERR_ARG, "truncated state");
+    const unsigned char* i = static_cast<const unsigned char*>(host) + sizeof(st);
+    TRBL_CUDA(cudaMemcpyAsync(Tm, i, sizeof(double) * mb * mb, cudaMemcpyHostToDevice, s));
+    i += sizeof(double) * mb * mb;
+    TRBL_CUDA(cudaMemcpyAsync(beta, i, sizeof(double) * q * q, cudaMemcpyHostToDevice, s));
+    i += sizeof(double) * q * q;
+    TRBL_CUDA(cudaMemcpyAsync(Vk, i, sizeof(T) * D * q, cudaMemcpyHostToDevice, s));
+    i += sizeof(T) * D * q;
+    TRBL_CUDA(cudaMemcpy2DAsync(basis, sizeof(T) * mb, i, sizeof(T) * st.nb, sizeof(T) * st.nb, size_t(D),
+                                cudaMemcpyHostToDevice, s));
+    TRBL_CUDA(cudaStreamSynchronize(s));
+    nb = st.nb;
+    iter = st.iter;
+    restarts = st.restarts;
+    conv = st.conv;
+    reseed = st.reseed;
+    normH = st.normH;
+    since_check_ms = st.since_check_ms;
+    last_check_ms = st.last_check_ms;
+    ms_apply = st.ms[0];
+    ms_orth = st.ms[1];
+    ms_qr = st.ms[2];
+    ms_ritz = st.ms[3];
+    ms_restart = st.ms[4];
+    done = have_ritz = finished = false;
+    return TRBL_OK;
+  }
+
   // Ritz values, vectors and true residuals of the current basis.
   int finish(double* evals, double* resid, void* evecs, trbl_stats* st) {
     const int status = done ? TRBL_OK : TRBL_ERR_NOCONV;
@@ -979,6 +1071,9 @@ struct SolverBase {
   virtual size_t block_bytes() = 0;
   virtual bool is_done() = 0;
   virtual int iterations() = 0;
+  virtual size_t state_bytes() = 0;
+  virtual int save(void* host, int64_t bytes) = 0;
+  virtual int load(const void* host, int64_t bytes) = 0;
 };
 
 template <typename T>
@@ -999,6 +1094,9 @@ struct SolverImpl : SolverBase {
   size_t block_bytes() override { return sizeof(T) * size_t(S.D) * S.q; }
   bool is_done() override { return S.done; }
   int iterations() override { return S.iter; }
+  size_t state_bytes() override { return S.state_bytes(); }
+  int save(void* host, int64_t bytes) override { return S.save(host, bytes); }
+  int load(const void* host, int64_t bytes) override { return S.load(host, bytes); }
 };
 
 }  // namespace
@@ -1449,6 +1547,25 @@ extern "C" int trbl_solver_step_host(trbl_solver* sv, const void* block_in, void
     TRBL_CUDA(cudaStreamSynchronize(sv->stream));
   }
   return TRBL_OK;
+}
+
+extern "C" int trbl_solver_state_bytes(trbl_solver* sv, int64_t* bytes) {
+  clear_error();
+  if (!sv || !sv->impl || !bytes) return fail(TRBL_ERR_ARG, "null argument");
+  *bytes = int64_t(sv->impl->state_bytes());
+  return TRBL_OK;
+}
+
+extern "C" int trbl_solver_save(trbl_solver* sv, void* host, int64_t bytes) {
+  clear_error();
+  if (!sv || !sv->impl) return fail(TRBL_ERR_ARG, "null solver");
+  return sv->impl->save(host, bytes);
+}
+
+extern "C" int trbl_solver_load(trbl_solver* sv, const void* host, int64_t bytes) {
+  clear_error();
+  if (!sv || !sv->impl) return fail(TRBL_ERR_ARG, "null solver");
+  return sv->impl->load(host, bytes);
 }
 
 extern "C" int trbl_solver_block(trbl_solver* sv, void** block, int64_t* bytes) {
