@@ -41,7 +41,8 @@ extern "C" {
 #define TRBL_ERR_ARG 1       /* invalid argument (null pointer, size, layout) */
 #define TRBL_ERR_CUDA 2      /* a CUDA runtime or library call failed */
 #define TRBL_ERR_OOM 3       /* device or host allocation failed */
-#define TRBL_ERR_BREAKDOWN 4 /* block QR found a rank-deficient block it could not repair */
+#define TRBL_ERR_BREAKDOWN 4 /* block QR found a rank-deficient block it could not repair, or the block
+                                or T holds NaN or Inf (for example from a caller's block) */
 #define TRBL_ERR_NOCONV 5    /* iteration limit reached; partial results returned */
 
 #define TRBL_F32 0 /* IEEE binary32 vectors */
@@ -114,9 +115,10 @@ int trbl_basis_export_jumps(const trbl_basis* b, int species, int32_t* tgt, int3
  *   VBB[nB^4]   the same for species B;
  *   VAB[nA*nB*nA*nB] coefficient of a+_a b+_b b_d a_c, index
  *               ((a*nB+b)*nA+c)*nB+d.
- * Coefficients that do not conserve 2m are ignored.  The caller keeps b
- * alive while *out exists.  Errors: TRBL_ERR_ARG, TRBL_ERR_OOM,
- * TRBL_ERR_CUDA. */
+ * Coefficients that do not conserve 2m are ignored, but every entry must be
+ * finite.  The caller keeps b alive while *out exists.  Errors:
+ * TRBL_ERR_ARG (null argument, or a NaN or Inf entry in any array),
+ * TRBL_ERR_OOM, TRBL_ERR_CUDA. */
 int trbl_hamiltonian_create(const trbl_basis* b, const double* h1A, const double* h1B,
                             const double* VAA, const double* VBB, const double* VAB,
                             trbl_hamiltonian** out);

@@ -12,6 +12,7 @@
 //   locates the target by binary search (App. B.1), which is what `find`
 //   does here, once, at build time.
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -379,6 +380,18 @@ extern "C" int trbl_hamiltonian_create(const trbl_basis* b, const double* h1A, c
   if (!out) return fail(TRBL_ERR_ARG, "out is null");
   *out = nullptr;
   if (!b || !h1A || !h1B || !VAA || !VBB || !VAB) return fail(TRBL_ERR_ARG, "null argument");
+  {
+    const size_t nA = size_t(b->sp[0].n), nB = size_t(b->sp[1].n);
+    const struct {
+      const double* x;
+      size_t n;
+      const char* name;
+    } arrays[] = {{h1A, nA * nA, "h1A"}, {h1B, nB * nB, "h1B"}, {VAA, nA * nA * nA * nA, "VAA"},
+                  {VBB, nB * nB * nB * nB, "VBB"}, {VAB, nA * nB * nA * nB, "VAB"}};
+    for (const auto& a : arrays)
+      for (size_t i = 0; i < a.n; ++i)
+        if (!std::isfinite(a.x[i])) return fail(TRBL_ERR_ARG, "%s[%zu] is not finite", a.name, i);
+  }
   trbl_hamiltonian* h = new (std::nothrow) trbl_hamiltonian();
   if (!h) return fail(TRBL_ERR_OOM, "host allocation failed");
   h->b = b;

@@ -525,7 +525,11 @@ struct Solver {
     TRBL_CUDA(cudaMemcpyAsync(hbuf, G, sizeof(double) * q * q, cudaMemcpyDeviceToHost, s));
     TRBL_CUDA(cudaStreamSynchronize(s));
     double cmax = 0.0;
-    for (int j = 0; j < q; ++j) cmax = std::max(cmax, std::sqrt(std::max(hbuf[j * q + j], 0.0)));
+    for (int j = 0; j < q; ++j) {
+      if (!std::isfinite(hbuf[j * q + j]))
+        return fail(TRBL_ERR_BREAKDOWN, "non-finite values in the Lanczos block (NaN or Inf in H or the vectors)");
+      cmax = std::max(cmax, std::sqrt(std::max(hbuf[j * q + j], 0.0)));
+    }
     const double thr = std::max(tau * normH, (dtype == TRBL_F64 ? 1e-13 : 1e-6) * cmax);
     for (int j = 0; j < q; ++j) {
       T* wj = W + j;
@@ -578,6 +582,8 @@ struct Solver {
     TRBL_CUDA(cudaMemcpyAsync(hflags + kInfo, devinfo, sizeof(int), cudaMemcpyDeviceToHost, s));
     TRBL_CUDA(cudaStreamSynchronize(s));
     if (hflags[kInfo] != 0) return fail(TRBL_ERR_CUDA, "syevd info=%d", hflags[kInfo]);
+    for (int i = 0; i < nb; ++i)
+      if (!std::isfinite(hbuf[i])) return fail(TRBL_ERR_BREAKDOWN, "non-finite Ritz values (NaN or Inf in T)");
     const double est = std::max(std::fabs(hbuf[0]), std::fabs(hbuf[nb - 1]));
     if (p->normH <= 0.0) normH = std::max(normH, est);
     return TRBL_OK;

@@ -87,9 +87,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 
 // Round an FP32 value to the nearest TF32 value (10 explicit mantissa bits;
 // ties away from zero): add half of the dropped 13-bit unit to the
-// sign-magnitude pattern and clear the dropped bits.
+// sign-magnitude pattern and clear the dropped bits.  A NaN is returned as
+// it is: the addition would carry a high payload into the sign bit and turn
+// the NaN into -0 (the usual all-ones payload does exactly that), so NaN
+// data would silently become zeros.
 __device__ __forceinline__ float tf32_round(float x) {
-  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+  const uint32_t u = __float_as_uint(x);
+  if ((u & 0x7FFFFFFFu) > 0x7F800000u) return x;
+  return __uint_as_float((u + 0x1000u) & 0xFFFFE000u);
 }
 
 // x = hi + lo with hi, lo TF32: |x - hi - lo| <= 2^-22 |x|.

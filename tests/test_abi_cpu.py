@@ -89,6 +89,19 @@ def test_errors_are_reported():
         trbl.Basis(sp, 2, sp, 2, 41)  # no determinants reach 2M = 41
 
 
+def test_non_finite_coefficients_are_rejected_before_any_upload():
+    sp = synth.make_space(synth.SPACE12_SHELLS)
+    inter = synth.draw_interaction(sp, sp, 3)
+    tb = trbl.Basis(sp, 2, sp, 2, 0)
+    for name, val in (("h1A", np.nan), ("VBB", np.inf), ("VAB", -np.inf)):
+        arrs = {k: getattr(inter, k).copy() for k in ("h1A", "h1B", "VAA", "VBB", "VAB")}
+        arrs[name].flat[7] = val
+        with pytest.raises(trbl.TrblError) as e:
+            trbl.Hamiltonian(tb, arrs["h1A"], arrs["h1B"], arrs["VAA"], arrs["VBB"], arrs["VAB"])
+        assert e.value.code == trbl.TRBL_ERR_ARG
+        assert name + "[7] is not finite" in str(e.value)
+
+
 def test_parameter_order_matches_generator():
     for shells in (synth.SPACE12_SHELLS, synth.SPACE20_SHELLS, synth.TABLE1_SHELLS):
         sp = synth.make_space(shells)

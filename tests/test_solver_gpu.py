@@ -134,3 +134,17 @@ def test_solve_reports_noconv_and_bad_args(small):
     assert e.value.code == trbl.TRBL_ERR_ARG
     with pytest.raises(trbl.TrblError):
         trbl.solve(th, 30, 8, 40, w.tol)  # max_basis < nev + 2q
+
+
+@pytest.mark.parametrize("precision,dt", [(trbl.TRBL_PREC_F64, torch.float64), (trbl.TRBL_PREC_MIXED, torch.float32)])
+def test_non_finite_block_is_reported(small, precision, dt):
+    """A caller's block holding NaN (trbl_solver_step_host) ends the step with
+    TRBL_ERR_BREAKDOWN before any NaN reaches the eigensolver."""
+    w, H, ev, U, th = small
+    sv = trbl.Solver(th, 4, 4, 40, 1e-8, precision=precision, check_every=1)
+    _, nbytes = sv.block()
+    blk = torch.full((nbytes // (8 if dt == torch.float64 else 4),), float("nan"), dtype=dt)
+    with pytest.raises(trbl.TrblError) as e:
+        sv.step_host(blk, None)
+    assert e.value.code == trbl.TRBL_ERR_BREAKDOWN
+    assert "non-finite" in str(e.value)

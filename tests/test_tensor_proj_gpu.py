@@ -87,6 +87,27 @@ def test_gram_diagonal_is_unbiased(tensor_cores):
     assert np.abs(rel).max() <= 3e-6, np.abs(rel).max()
 
 
+def test_tensor_core_paths_propagate_nan():
+    """A NaN with the all-ones payload that CUDA's arithmetic produces, placed
+    in W, makes exactly its column of C = B^T W NaN; placed in In, exactly
+    its row of the update.  (Rounding to TF32 by adding half a unit to the
+    bit pattern carries such a payload into the sign bit and turns the NaN
+    into -0, which would hide it.)"""
+    nan = torch.tensor([0x7FFFFFFF], dtype=torch.int32).view(torch.float32)[0]
+    D = 4097
+    B = _f32(synth.random_block(D, 64, 51))
+    W = _f32(synth.random_block(D, 32, 52))
+    W[100, 5] = nan
+    C = trbl.block_dot(_dev_ld4(B), _dev_ld4(W), tensor_cores=True).cpu().numpy()
+    assert np.all(np.isnan(C[:, 5])) and np.all(np.isfinite(np.delete(C, 5, axis=1)))
+    In = _f32(synth.random_block(D, 300, 53))
+    In[7, 3] = nan
+    U = synth.random_block(300, 16, 54)
+    Out = trbl.block_update(_dev_ld4(In), torch.from_numpy(U), torch.zeros((D, 16), device="cuda"), 1.0, 0.0,
+                            algo=trbl.TRBL_PROJ_TENSOR).cpu().numpy()
+    assert np.all(np.isnan(Out[7])) and np.all(np.isfinite(np.delete(Out, 7, axis=0)))
+
+
 def test_block_dot_tc_rejects_unsupported_shapes():
     B = torch.zeros((100, 8), device="cuda")
     W = torch.zeros((100, 40), device="cuda")
