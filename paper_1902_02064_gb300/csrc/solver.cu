@@ -1124,7 +1124,7 @@ struct BatchDriver {
   using clock = std::chrono::steady_clock;
   std::vector<Solver<T>*> sets;
   trbl_params prm{};
-  cudaStream_t s = nullptr;         // the driver's stream (capture origin)
+  cudaStream_t s = nullptr;         // the batch's own stream (capture origin)
   std::vector<cudaStream_t> ss;     // one stream per set
   std::vector<cudaEvent_t> ev_done;  // end of a set's host-driven work
   int nset = 0, nwork = 0, dtype = 0, device = 0, nthreads = 1;
