@@ -6,6 +6,7 @@ dimensions printed in the paper for the 20Ne sd space (640, App. C Fig. 8),
 and 112Sn (6,210,638, Sec. IV C); closed forms for the number of one-body
 jumps.
 """
+import itertools
 import os
 
 import pytest
@@ -93,6 +94,36 @@ def test_one_body_jump_closed_form():
     for k in (1, 2, 3, 4):
         ndet = len(ob.species_determinants(sp.twom, k))
         assert ob.one_body_jump_count(sp.twom, k) == ndet * k * (sp.n - k)
+
+
+def _targets_by_moves(twom, k):
+    """Like-particle targets counted by explicit moves: from every determinant,
+    one particle i -> j with m_i = m_j, or a pair {i, j} -> {a, b} with
+    m_i + m_j = m_a + m_b (App. B.1: the states a one- or two-body term
+    reaches inside one M block).  Distinct moves reach distinct states."""
+    n = len(twom)
+    cnt = 0
+    for occ in itertools.combinations(range(n), k):
+        empty = [x for x in range(n) if x not in occ]
+        cnt += sum(1 for i in occ for j in empty if twom[i] == twom[j])
+        cnt += sum(1 for i, j in itertools.combinations(occ, 2) for a, b in itertools.combinations(empty, 2)
+                   if twom[i] + twom[j] == twom[a] + twom[b])
+    return cnt
+
+
+@pytest.mark.parametrize("shells,k", [(synth.SPACE12_SHELLS, 2), (synth.SPACE12_SHELLS, 4),
+                                      (synth.SPACE20_SHELLS, 2), (synth.SPACE20_SHELLS, 3)])
+def test_same_species_targets_by_moves(shells, k):
+    """The xor-popcount count of the oracle equals the count of explicit
+    moves; with 2 particles every other pair state of equal M is a target."""
+    sp = synth.make_space(shells)
+    assert ob.same_species_targets(sp.twom, k) == _targets_by_moves(sp.twom, k)
+    if k == 2 and sp.n == 12:
+        dets = ob.species_determinants(sp.twom, 2)
+        per_m = {}
+        for m, _ in dets:
+            per_m[m] = per_m.get(m, 0) + 1
+        assert ob.same_species_targets(sp.twom, 2) == sum(c * (c - 1) for c in per_m.values())
 
 
 def test_species_order_is_M_then_value():
