@@ -62,11 +62,6 @@ def lanczos(matvec: Callable[[np.ndarray], np.ndarray], D: int, nev: int,
     raise RuntimeError("Lanczos did not converge in %d iterations" % max_iter)
 
 
-def spectral_norm_dense(H) -> float:
-    ev = np.linalg.eigvalsh(H.toarray() if hasattr(H, "toarray") else H)
-    return float(max(abs(ev[0]), abs(ev[-1])))
-
-
 def extreme_eigenvalues(matvec, D: int, seed_vec: np.ndarray, tol=1e-12, normH_guess=1.0,
                         max_iter: int = 600) -> Tuple[float, float]:
     """Lowest and highest eigenvalue by Algorithm 1 on H and on -H."""

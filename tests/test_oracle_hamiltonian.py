@@ -43,6 +43,27 @@ def test_bitstring_equals_jordan_wigner(kA, kB, twoM):
     assert np.abs(H - HJ).max() < 1e-12
 
 
+def test_one_body_jumps_match_jordan_wigner_and_count():
+    """The oracle's one-body jump list of one species (App. B.2): every entry
+    (S', S, a, c, sign) equals the Jordan-Wigner matrix element
+    <S'|c+_a c_c|S>, and there are N_det k (n - k + 1) of them (c occupied,
+    a empty or a = c)."""
+    sp = synth.make_space(SMALL_SHELLS)
+    n = sp.n
+    c = jw.annihilators(n)
+    cd = [x.T.tocsr() for x in c]
+    for k in (1, 2, 3):
+        dets = ob.species_determinants(sp.twom, k)
+        J = oh.one_body_jumps(sp.twom, k)
+        assert len(J) == len(dets) * k * (n - k + 1)
+        rows = [jw.occupation_index([b >> j & 1 for j in range(n)], n) for _, b in dets]
+        ops = {}
+        for t, src, a, cc, sign in J:
+            if (a, cc) not in ops:
+                ops[(a, cc)] = (cd[a] @ c[cc]).tocsr()
+            assert ops[(a, cc)][rows[t], rows[src]] == sign
+
+
 def test_jordan_wigner_anticommutation():
     c = jw.annihilators(4)
     for i in range(4):
