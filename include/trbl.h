@@ -27,6 +27,8 @@
  *   state (iA, iB) has index offset + iA * N_B + iB.
  * - A block of vectors is row-major: row i (basis state i) holds q values,
  *   rows ld elements apart (ld >= q).
+ * - One CUDA device per process: kernel attributes and the SM count are set
+ *   up once, on the device current at the first call that launches work.
  */
 #ifndef TRBL_H
 #define TRBL_H
