@@ -99,6 +99,28 @@ class ProductBasis:
             s: i for i, s in enumerate(self.states)}
 
 
+def partitions(twomA, orbitA, kA, twomB, orbitB, kB, twoM):
+    """Partitions Gamma = (N^A, N^B, 2M_A) of App. A: orbit occupation
+    vectors of the two species and the first species' 2M for which both
+    species have determinants with 2M_A + 2M_B = twoM.  Returns a dict
+    Gamma -> number of basis states in it (the product of the two species'
+    determinant counts)."""
+    def occupations(twom, orbit, k):
+        norb = max(orbit) + 1 if len(orbit) else 0
+        cnt: Dict[Tuple[Tuple[int, ...], int], int] = {}
+        for occ in itertools.combinations(range(len(twom)), k):
+            N = [0] * norb
+            for i in occ:
+                N[orbit[i]] += 1
+            key = (tuple(N), sum(twom[i] for i in occ))
+            cnt[key] = cnt.get(key, 0) + 1
+        return cnt
+    PA = occupations(twomA, orbitA, kA)
+    PB = occupations(twomB, orbitB, kB)
+    return {(NA, NB, mA): cA * cB for (NA, mA), cA in PA.items() for (NB, mB), cB in PB.items()
+            if mA + mB == twoM}
+
+
 def _groups(dets):
     """2M -> (first index, count) for a sorted determinant list."""
     g: Dict[int, List[int]] = {}

@@ -2,9 +2,10 @@
 
 Sources: Table I (App. A) for the bit representation and its order; the
 dimensions printed in the paper for the 20Ne sd space (640, App. C Fig. 8),
-24Mg sd space (28,503, App. C Fig. 9), 48Cr pf space (1,963,461, Sec. IV A)
-and 112Sn (6,210,638, Sec. IV C); closed forms for the number of one-body
-jumps.
+24Mg sd space (28,503, App. C Fig. 9), 48Cr pf space (1,963,461, Sec. IV A),
+112Sn (6,210,638, Sec. IV C) and 56Ni (1,087,455,228, App. B); the partition
+counts of App. C (162 for 20Ne, 1020 for 24Mg); closed forms for the number
+of one-body jumps.
 """
 import itertools
 import os
@@ -87,6 +88,25 @@ def test_generating_function_paper_dimensions():
     sn = synth.make_space(((7, 0), (5, 0), (3, 0), (1, 0), (11, 0)))
     parity = [1 if o == 4 else 0 for o in sn.orbit]
     assert ob.dimension_by_generating_function((), 0, sn.twom, 12, 0, parity, 0) == 6210638
+
+
+@pytest.mark.parametrize("k,want", [(2, 162), (4, 1020)])
+def test_paper_partition_counts_sd(k, want):
+    """The sd-shell partitions (N^p, N^n, M^p) the paper counts for 20Ne
+    (162) and 24Mg (1020) in App. C; their states add up to the M-scheme
+    dimension."""
+    sp = synth.make_space(synth.SPACE12_SHELLS)
+    P = ob.partitions(sp.twom, sp.orbit, k, sp.twom, sp.orbit, k, 0)
+    assert len(P) == want
+    assert sum(P.values()) == ob.ProductBasis(sp.twom, k, sp.twom, k, 0).dim
+
+
+def test_generating_function_56Ni():
+    """56Ni in the pf shell, 8 + 8 particles, M = 0: 1,087,455,228 states
+    (the dimension the paper gives when it motivates the on-the-fly
+    product, App. B)."""
+    sp20 = synth.make_space(synth.SPACE20_SHELLS)
+    assert ob.dimension_by_generating_function(sp20.twom, 8, sp20.twom, 8, 0) == 1087455228
 
 
 def test_one_body_jump_closed_form():
