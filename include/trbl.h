@@ -222,8 +222,10 @@ int trbl_block_update(const void* In, int64_t ldi, int K, const double* U, int64
  * fewer row chunks, never more scratch.
  *
  * The first call on a device looks up the scratch array's device address
- * (with that device current); make that first call before any stream
- * capture.  All calls on a device share the one array: calls whose
+ * (with that device current) and loads every kernel this entry point can
+ * launch, for both element types and every q, so that CUDA's lazy module
+ * loading takes no device memory during a later call; make that first call
+ * before any stream capture.  All calls on a device share the one array: calls whose
  * executions overlap on the GPU (different streams, or different host
  * threads) race and give wrong results.  Every call overwrites the part of
  * the scratch it reads, so no clearing is needed between calls. */

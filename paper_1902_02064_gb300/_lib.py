@@ -13,6 +13,7 @@ TRBL_OK, TRBL_ERR_ARG, TRBL_ERR_CUDA, TRBL_ERR_OOM, TRBL_ERR_BREAKDOWN, TRBL_ERR
 TRBL_F32, TRBL_F64 = 0, 1
 TRBL_PREC_F64, TRBL_PREC_MIXED = 1, 2
 TRBL_PROJ_TENSOR, TRBL_PROJ_CUDA_CORE = 0, 1
+TRBL_NOALLOC_SCRATCH_BYTES = 8 << 20  # include/trbl.h
 
 
 class TrblError(RuntimeError):
@@ -412,14 +413,15 @@ class Solver:
 
     def __init__(self, h: Hamiltonian, nev: int, q: int, max_basis: int, tol: float,
                  precision: int = TRBL_PREC_F64, keep: int = 0, check_every: int = 0, seed: int = 1,
-                 normH: float = 0.0, stream=None, projections: int = TRBL_PROJ_TENSOR):
+                 normH: float = 0.0, stream=None, projections: int = TRBL_PROJ_TENSOR, max_iter: int = 0):
         import torch
         self.h = h
         self.nev, self.q, self.precision = nev, q, precision
         self.handle = None
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
-        self.params = _params(nev, q, max_basis, tol, precision, keep, 0, check_every, seed, normH, projections)
+        self.params = _params(nev, q, max_basis, tol, precision, keep, max_iter, check_every, seed, normH,
+                              projections)
         self.handle = trbl_solver_create(h.handle, self.params, s.cuda_stream)
 
     def step(self) -> int:

@@ -546,6 +546,21 @@ int block_dot_capped(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, in
   return fail(TRBL_ERR_ARG, "block_dot: q=%d > 64", q);
 }
 
+int block_dot_capped_load_kernels() {
+  // cudaFuncGetAttributes loads a kernel that lazy module loading has not
+  // loaded yet, so no later block_dot_capped call loads (and allocates) one.
+  cudaFuncAttributes a;
+  const void* fns[] = {
+      reinterpret_cast<const void*>(block_dot_kernel<float, 4>),   reinterpret_cast<const void*>(block_dot_kernel<float, 8>),
+      reinterpret_cast<const void*>(block_dot_kernel<float, 16>),  reinterpret_cast<const void*>(block_dot_kernel<float, 32>),
+      reinterpret_cast<const void*>(block_dot_kernel<float, 64>),  reinterpret_cast<const void*>(block_dot_kernel<double, 4>),
+      reinterpret_cast<const void*>(block_dot_kernel<double, 8>),  reinterpret_cast<const void*>(block_dot_kernel<double, 16>),
+      reinterpret_cast<const void*>(block_dot_kernel<double, 32>), reinterpret_cast<const void*>(block_dot_kernel<double, 64>),
+      reinterpret_cast<const void*>(reduce_partials_kernel)};
+  for (const void* f : fns) TRBL_CUDA(cudaFuncGetAttributes(&a, f));
+  return TRBL_OK;
+}
+
 template int block_dot_capped<float>(const float*, int64_t, int, const float*, int64_t, int, int64_t, double*,
                                      double*, size_t, int, cudaStream_t);
 template int block_dot_capped<double>(const double*, int64_t, int, const double*, int64_t, int, int64_t, double*,

@@ -31,6 +31,9 @@ template <typename T>
 int block_dot_capped(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, int64_t D, double* C,
                      double* partial, size_t partial_bytes, int sm_count, cudaStream_t s);
 
+// Loads (under lazy module loading) every kernel block_dot_capped can launch.
+int block_dot_capped_load_kernels();
+
 // Out[:, 0:n] = alpha * In[:, 0:K] U[K x n] + beta * Out (U FP64 row-major, ld ldu).
 // In and Out must not overlap.
 template <typename T>

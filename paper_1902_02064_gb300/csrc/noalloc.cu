@@ -4,8 +4,11 @@
 // device array of TRBL_NOALLOC_SCRATCH_BYTES.  Host code cannot use the
 // array's name as a device address, so the first call on each device looks
 // the address up with cudaGetSymbolAddress (that device current) and caches
-// it; later calls on that device reuse it.  Calls that overlap on one device
-// share the array and race.
+// it; later calls on that device reuse it.  The same first call loads every
+// kernel the entry point can launch (both element types, every block-width
+// bucket, the reduction), so that lazy module loading never loads one, and
+// takes device memory for it, during a later call.  Calls that overlap on
+// one device share the array and race.
 #include <mutex>
 
 #include "blas.cuh"
@@ -31,6 +34,8 @@ int scratch_on(int dev, double** addr, int* sms) {
     int n = 0;
     e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    const int rc = block_dot_capped_load_kernels();
+    if (rc) return rc;
     g_sm_count[dev] = n > 0 ? n : 1;
     g_scratch_addr[dev] = static_cast<double*>(p);
   }

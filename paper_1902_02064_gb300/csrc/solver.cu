@@ -655,6 +655,10 @@ struct Solver {
   double since_check_ms = 0, last_check_ms = 0;  // adaptive Rayleigh-Ritz cadence
   int nb = 0, iter = 0, restarts = 0, conv = 0;
   bool done = false, have_ritz = false, finished = false;
+  // T[0:nb, 0:nb] is complete (no block appended since its last Rayleigh-
+  // Ritz step) but its eigenpairs are not on the device: set by load() for a
+  // state saved in that condition, cleared by the next step.
+  bool t_complete = false;
 
   // Start block: seeded random D x q, orthonormalised (Alg. 4, first line).
   int init() {
@@ -680,6 +684,7 @@ struct Solver {
       return TRBL_OK;
     }
     const int max_iter = p->max_iter > 0 ? p->max_iter : 100000;
+    t_complete = false;
     trace("iter %d nb %d", iter, nb);
     tm.rec(0, s);
     TRY(apply(Vk, W));
@@ -818,10 +823,13 @@ struct Solver {
   // ---- checkpoint: the state between block steps ----
   // Header, then T (mb x mb FP64), beta (q x q FP64, for the residual
   // estimates of a finish right after a load), V_k (D x q) and the basis
-  // (D x nb, packed), all in host memory.
+  // (D x nb, packed), all in host memory.  `complete` is 1 when T[0:nb,
+  // 0:nb] had its Rayleigh-Ritz step without a block appended after it (a
+  // step that stopped at max_iter): a finish then uses all nb rows, as the
+  // uninterrupted solver does.
   struct State {
     uint64_t magic;
-    int32_t version, dtype, q, mb, ls, nb, iter, restarts, conv, pad;
+    int32_t version, dtype, q, mb, ls, nb, iter, restarts, conv, complete;
     int64_t D;
     uint64_t reseed;
     double normH, since_check_ms, last_check_ms, ms[5];
@@ -847,6 +855,7 @@ struct Solver {
     st.iter = iter;
     st.restarts = restarts;
     st.conv = conv;
+    st.complete = (have_ritz || t_complete) ? 1 : 0;
     st.D = D;
     st.reseed = reseed;
     st.normH = normH;
@@ -878,6 +887,7 @@ struct Solver {
       return fail(TRBL_ERR_ARG, "state saved with other sizes (D %lld, q %d, max_basis %d, keep %d, precision)",
                   (long long)st.D, st.q, st.mb, st.ls);
     if (st.nb < q || st.nb > mb) return fail(TRBL_ERR_ARG, "corrupt state (basis size %d)", st.nb);
+    if (st.complete != 0 && st.complete != 1) return fail(TRBL_ERR_ARG, "corrupt state (flag %d)", st.complete);
     if (size_t(bytes) < state_bytes_for(st.nb)) return fail(TRBL_ERR_ARG, "truncated state");
     const unsigned char* i = static_cast<const unsigned char*>(host) + sizeof(st);
     TRBL_CUDA(cudaMemcpyAsync(Tm, i, sizeof(double) * mb * mb, cudaMemcpyHostToDevice, s));
@@ -903,6 +913,7 @@ struct Solver {
     ms_ritz = st.ms[3];
     ms_restart = st.ms[4];
     done = have_ritz = finished = false;
+    t_complete = st.complete == 1;
     return TRBL_OK;
   }
 
@@ -913,7 +924,7 @@ struct Solver {
     // After an append or a restart the basis holds one more block than T's
     // last Rayleigh-Ritz step saw; the Ritz pairs below use the block
     // diagonal part of T that is complete (rows 0 .. nb - q).
-    int nr = have_ritz ? nb : nb - q;
+    int nr = (have_ritz || t_complete) ? nb : nb - q;
     if (!have_ritz) TRY(ritz(nr));
     const int n = std::min(nev, nr);
     for (int i = 0; i < n; ++i) evals[i] = hbuf[i];

@@ -31,6 +31,13 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(L, n), n
 
 
+def test_python_constants_match_the_header():
+    txt = open(HEADER).read()
+    m = re.search(r"#define TRBL_NOALLOC_SCRATCH_BYTES \((\d+)u << (\d+)\)", txt)
+    assert m, "TRBL_NOALLOC_SCRATCH_BYTES not found in the header"
+    assert trbl.TRBL_NOALLOC_SCRATCH_BYTES == int(m.group(1)) << int(m.group(2))
+
+
 @pytest.mark.parametrize("shells,kA,kB,twoM", [
     (synth.SPACE12_SHELLS, 2, 2, 0), (synth.SPACE12_SHELLS, 4, 4, 0), (synth.SPACE12_SHELLS, 3, 2, 1),
     (synth.SPACE12_SHELLS, 0, 2, 0), (synth.SPACE12_SHELLS, 1, 1, 4), (synth.TABLE1_SHELLS, 3, 0, 1),

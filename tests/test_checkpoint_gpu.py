@@ -84,3 +84,24 @@ def test_converged_solver_is_not_saved():
     with pytest.raises(trbl.TrblError) as e:
         sv.save()
     assert e.value.code == trbl.TRBL_ERR_ARG
+
+
+@pytest.mark.parametrize("precision", [trbl.TRBL_PREC_F64, trbl.TRBL_PREC_MIXED])
+def test_state_saved_at_max_iter_finishes_like_the_original(medium, precision):
+    """A step that stops at max_iter runs Rayleigh-Ritz on the whole T and
+    appends nothing; a state saved there and finished in another solver
+    gives the Ritz pairs the original solver's finish gives (all nb rows of
+    T, not nb - q)."""
+    tb, th = medium
+    mk = lambda: trbl.Solver(th, 8, 8, 64, 1e-14, precision=precision, check_every=0, seed=5, max_iter=7)
+    a = mk()
+    for _ in range(7):
+        a.step()
+    state = a.save()
+    b = mk()
+    b.load(state)
+    ea, ra, Xa, sa = a.finish(raise_on_noconv=False)
+    eb, rb, Xb, sb = b.finish(raise_on_noconv=False)
+    assert sa["iterations"] == sb["iterations"] == 7
+    assert np.array_equal(ea, eb) and np.array_equal(ra, rb)
+    assert torch.equal(Xa, Xb)
