@@ -628,7 +628,8 @@ def run_apply_only(args):
     dt = torch.float64 if args.fp64 else torch.float32
     if args.rows:
         tune_ms, tune_rows = None, args.rows
-        trbl.apply_set_rows(th, args.rows)
+        kern = trbl.TRBL_APPLY_GROUPED if args.kernel == "grouped" else trbl.TRBL_APPLY_FAST
+        trbl.apply_set_shape(th, kern, args.rows, args.bps)
     else:
         tune_ms, tune_rows = trbl.apply_autotune(th, q, trbl.TRBL_F64 if args.fp64 else trbl.TRBL_F32)
     g = torch.Generator(device="cuda")
@@ -652,7 +653,7 @@ def run_apply_only(args):
     print(json.dumps({"workload": args.apply_only, "dim": tb.dim, "q": q, "dtype": str(dt),
                       "ms_per_apply": ms, "gnzq_per_s": nnz * q / (ms * 1e-3) / 1e9,
                       "structural_nnz": nnz, "slab_rows_R": R, "algorithmic_bytes": b_slab,
-                      "rows_per_item": tune_rows, "autotune_ms": tune_ms,
+                      "rows_per_item": tune_rows, "autotune_ms": tune_ms, "shape": trbl.apply_get_shape(th),
                       "achieved_gbs": b_slab / (ms * 1e-3) / 1e9, "frac_of_measured_hbm": b_slab / (ms * 1e-3) / 1e9 / peak}),
           flush=True)
 
@@ -680,6 +681,10 @@ def main():
     ap.add_argument("--q", type=int, default=0)
     ap.add_argument("--rows", type=int, default=0,
                     help="--apply-only: fixed neutron rows per work item instead of the autotuner's choice")
+    ap.add_argument("--kernel", default="fast", choices=["fast", "grouped"],
+                    help="--apply-only with --rows: the product kernel")
+    ap.add_argument("--bps", type=int, default=8, choices=[6, 8],
+                    help="--apply-only with --rows: resident blocks per SM of the fast kernel")
     ap.add_argument("--fp64", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

@@ -314,18 +314,41 @@ int trbl_solve(const trbl_hamiltonian* h, const trbl_params* p, double* evals, d
 int trbl_solve_batch(const trbl_hamiltonian* const* hs, int nset, const trbl_params* p, double* evals,
                      double* resid, void* evecs, int* status, trbl_stats* stats, void* stream);
 
-/* Times the block product of h at block size q and dtype for the candidate
- * work-item sizes 16, 32, 64 and 128 neutron rows and keeps the fastest;
- * ms [4] (host, may be NULL) receives the average time per candidate and
- * *best_rows the choice.  Allocates two D x q scratch blocks for the timing.
- * Synchronises the stream. */
+/* Kernels of the block product (App. B; same elements, same arithmetic):
+ * TRBL_APPLY_GROUPED serves every q and both precisions; TRBL_APPLY_FAST is
+ * the FP32 kernel for q = 8, 16, 32 (16-byte aligned rows, D * ld < 2^31,
+ * at most 31 two-m transfer classes), with fewer instructions per generated
+ * element.  A product the chosen kernel cannot take runs on the grouped
+ * kernel. */
+#define TRBL_APPLY_GROUPED 0
+#define TRBL_APPLY_FAST 1
+/* Launch shapes trbl_apply_autotune times, in this order (kernel, neutron
+ * rows per work item, resident blocks per SM): grouped 16/32/64/128; fast
+ * 16/32/64 at 8 blocks per SM (32 registers a thread); fast 16/32/64 at 6
+ * blocks per SM (40 registers). */
+#define TRBL_TUNE_CANDIDATES 10
+
+/* Times the block product of h at block size q and dtype for each launch
+ * shape above that applies and keeps the fastest; ms [TRBL_TUNE_CANDIDATES]
+ * (host, may be NULL) receives the average time per candidate (NaN for a
+ * shape that does not apply to q and dtype) and *best_rows the chosen rows
+ * per work item (trbl_apply_get_shape gives the whole shape).  Allocates two
+ * D x q scratch blocks for the timing.  Synchronises the stream. */
 int trbl_apply_autotune(trbl_hamiltonian* h, int q, int dtype, float* ms, int* best_rows, void* stream);
 
-/* Sets the block product's launch shape to rows_per_item neutron rows per
- * work item (1..4096), as trbl_apply_autotune does with its choice; the
- * product's results do not depend on it.  Host only; not while a product
- * of h is running.  Errors: TRBL_ERR_ARG. */
+/* Sets the block product's rows per work item (1..4096), keeping its
+ * kernel; the product's results do not depend on it.  Host only; not while
+ * a product of h is running.  Errors: TRBL_ERR_ARG. */
 int trbl_apply_set_rows(trbl_hamiltonian* h, int rows_per_item);
+
+/* Sets the whole launch shape: kernel (TRBL_APPLY_GROUPED or
+ * TRBL_APPLY_FAST), rows per work item (1..4096) and resident blocks per SM
+ * of the fast kernel (6 or 8).  Same rules as trbl_apply_set_rows.  Errors:
+ * TRBL_ERR_ARG. */
+int trbl_apply_set_shape(trbl_hamiltonian* h, int kernel, int rows_per_item, int blocks_per_sm);
+
+/* The current launch shape (any output may be NULL).  Host only. */
+int trbl_apply_get_shape(const trbl_hamiltonian* h, int* kernel, int* rows_per_item, int* blocks_per_sm);
 
 /* Stepwise form of trbl_solve for callers that drive the iteration
  * themselves.  A solver owns its device workspace (basis of D x max_basis

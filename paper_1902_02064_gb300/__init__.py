@@ -13,7 +13,7 @@ App. B).
 from ._lib import (  # noqa: F401
     TRBL_OK, TRBL_ERR_ARG, TRBL_ERR_CUDA, TRBL_ERR_OOM, TRBL_ERR_BREAKDOWN, TRBL_ERR_NOCONV,
     TRBL_F32, TRBL_F64, TRBL_PREC_F64, TRBL_PREC_MIXED, TRBL_PROJ_TENSOR, TRBL_PROJ_CUDA_CORE, TRBL_NOALLOC_SCRATCH_BYTES,
-    TrblError,
+    TRBL_APPLY_GROUPED, TRBL_APPLY_FAST, TRBL_TUNE_CANDIDATES, TrblError,
     lib, library_path,
     trbl_basis_create, trbl_basis_destroy, trbl_basis_info, trbl_basis_export,
     trbl_basis_export_jumps, trbl_hamiltonian_create, trbl_hamiltonian_destroy,
@@ -22,6 +22,6 @@ from ._lib import (  # noqa: F401
     trbl_solver_create, trbl_solver_step, trbl_solver_step_host, trbl_solver_block,
     trbl_solver_stats, trbl_solver_destroy, trbl_solver_state_bytes, trbl_solver_save, trbl_solver_load,
     trbl_param_count, trbl_grad, arrays_from_theta, clusters_of, hf_gradient, hf_gradient_clusters, LowestEigenvalues,
-    solve_batch, apply_autotune, apply_set_rows,
+    solve_batch, apply_autotune, apply_set_rows, apply_set_shape, apply_get_shape,
     Basis, Hamiltonian, Solver, solve,
 )

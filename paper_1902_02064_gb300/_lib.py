@@ -14,6 +14,8 @@ TRBL_F32, TRBL_F64 = 0, 1
 TRBL_PREC_F64, TRBL_PREC_MIXED = 1, 2
 TRBL_PROJ_TENSOR, TRBL_PROJ_CUDA_CORE = 0, 1
 TRBL_NOALLOC_SCRATCH_BYTES = 8 << 20  # include/trbl.h
+TRBL_APPLY_GROUPED, TRBL_APPLY_FAST = 0, 1
+TRBL_TUNE_CANDIDATES = 10
 
 
 class TrblError(RuntimeError):
@@ -100,6 +102,8 @@ def lib():
                                        C.POINTER(C.c_int), C.POINTER(trbl_stats), _VP]),
         "trbl_apply_autotune": (C.c_int, [_VP, C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int), _VP]),
         "trbl_apply_set_rows": (C.c_int, [_VP, C.c_int]),
+        "trbl_apply_set_shape": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int]),
+        "trbl_apply_get_shape": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "trbl_kernel_launches": (C.c_longlong, []),
         "trbl_last_error": (C.c_char_p, []),
     }
@@ -634,10 +638,11 @@ def solve_batch(hs, nev: int, q: int, max_basis: int, tol: float, precision: int
 
 
 def apply_autotune(h: "Hamiltonian", q: int, dtype: int = TRBL_F32, stream=None):
-    """Times the product for 16/32/64/128 neutron rows per work item and keeps
-    the fastest; returns (times in ms, rows chosen)."""
+    """Times the product for each launch shape (kernel, neutron rows per work
+    item, blocks per SM; TRBL_TUNE_CANDIDATES of them, NaN where a shape does
+    not apply) and keeps the fastest; returns (times in ms, rows chosen)."""
     import torch
-    ms = (C.c_float * 4)()
+    ms = (C.c_float * TRBL_TUNE_CANDIDATES)()
     best = C.c_int()
     s = stream if stream is not None else torch.cuda.current_stream()
     _check(lib().trbl_apply_autotune(h.handle, int(q), int(dtype), ms, C.byref(best), s.cuda_stream))
@@ -645,8 +650,20 @@ def apply_autotune(h: "Hamiltonian", q: int, dtype: int = TRBL_F32, stream=None)
 
 
 def apply_set_rows(h: "Hamiltonian", rows_per_item: int):
-    """Sets the product's launch shape (neutron rows per work item)."""
+    """Sets the product's neutron rows per work item."""
     _check(lib().trbl_apply_set_rows(h.handle, int(rows_per_item)))
+
+
+def apply_set_shape(h: "Hamiltonian", kernel: int, rows_per_item: int, blocks_per_sm: int = 8):
+    """Sets the product's kernel, rows per work item and blocks per SM."""
+    _check(lib().trbl_apply_set_shape(h.handle, int(kernel), int(rows_per_item), int(blocks_per_sm)))
+
+
+def apply_get_shape(h: "Hamiltonian"):
+    """(kernel, rows per work item, blocks per SM) of the product."""
+    k, r, b = C.c_int(), C.c_int(), C.c_int()
+    _check(lib().trbl_apply_get_shape(h.handle, C.byref(k), C.byref(r), C.byref(b)))
+    return k.value, r.value, b.value
 
 
 def hf_gradient_clusters(h: "Hamiltonian", X, clusters, stream=None):

@@ -28,6 +28,7 @@
 //   the row is one task of a lane group, looping over the staged proton
 //   jumps of the opposite transfer.
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "internal.h"
@@ -336,6 +337,8 @@ int launch_grouped_batch(const void* hs_dev, const void* gs_dev, int nset, int n
 int launch_grouped(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, int64_t ldw, int q, int dtype,
                    cudaStream_t s) {
   if (!h->garena || h->g32.nwork == 0) return -1;
+  const int f = launch_fast(h, V, ldv, W, ldw, q, dtype, s);
+  if (f != -1) return f;
   if (dtype == TRBL_F64)
     return launch_typed<double>(h, h->d64, h->g64, static_cast<const double*>(V), ldv, static_cast<double*>(W), ldw,
                                 q, s);
@@ -402,10 +405,19 @@ int upload_grouped(trbl_hamiltonian* h) {
     return TRBL_OK;
   }
 
+  // species-B like-particle rows packed as (source local index, FP32 coefficient bits)
+  std::vector<int2> likeB(h->hsrc[1].size());
+  for (size_t e = 0; e < likeB.size(); ++e) {
+    const float c = float(h->hcoef[1][e]);
+    int bits;
+    std::memcpy(&bits, &c, 4);
+    likeB[e] = make_int2(h->hsrc[1][e], bits);
+  }
   size_t o_jB2 = 0;
   size_t o_c64 = (o_jB2 + jB2.size() * sizeof(int2) + 255) & ~size_t(255);
   size_t o_c32 = (o_c64 + cc.size() * 8 + 255) & ~size_t(255);
-  size_t total = o_c32 + cc32.size() * 4 + 256;
+  size_t o_lB = (o_c32 + cc32.size() * 4 + 255) & ~size_t(255);
+  size_t total = o_lB + likeB.size() * sizeof(int2) + 256;
   void* arena = nullptr;
   TRBL_CUDA(cudaMalloc(&arena, total));
   h->garena = arena;
@@ -413,6 +425,8 @@ int upload_grouped(trbl_hamiltonian* h) {
   TRBL_CUDA(cudaMemcpy(base + o_jB2, jB2.data(), jB2.size() * sizeof(int2), cudaMemcpyHostToDevice));
   TRBL_CUDA(cudaMemcpy(base + o_c64, cc.data(), cc.size() * 8, cudaMemcpyHostToDevice));
   TRBL_CUDA(cudaMemcpy(base + o_c32, cc32.data(), cc32.size() * 4, cudaMemcpyHostToDevice));
+  if (!likeB.empty())
+    TRBL_CUDA(cudaMemcpy(base + o_lB, likeB.data(), likeB.size() * sizeof(int2), cudaMemcpyHostToDevice));
   auto fill = [&](auto& g, size_t o_c) {
     using TT = typename std::remove_const<typename std::remove_pointer<decltype(g.ccoef)>::type>::type;
     g.maxP = maxP;
@@ -423,6 +437,8 @@ int upload_grouped(trbl_hamiltonian* h) {
   };
   fill(h->g64, o_c64);
   fill(h->g32, o_c32);
+  h->g64.likeB = nullptr;
+  h->g32.likeB = reinterpret_cast<const int2*>(base + o_lB);
   return set_work_items(h, kRowsPerItem);
 }
 

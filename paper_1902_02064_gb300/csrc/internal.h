@@ -97,8 +97,9 @@ struct DevG {
   const int4* work;     // (target A determinant, block, first neutron row, row count)
   int nwork;
   int maxP, maxQ, maxK; // per-target proton jumps, like-particle A sources, coefficient row length
-  const int2* jB2;      // neutron jumps: (source local index, (k << 1) | negative), k = pair index in its 2m-transfer class
+  const int2* jB2;      // neutron jumps: (source local index, (k << 9) | (transfer << 1) | negative), k = pair index in its 2m-transfer class
   const T* ccoef;       // ccoef[(a*nA + c) * maxK + k] = V^AB_{a b_k, c d_k} for the class of transfer m_c - m_a
+  const int2* likeB;    // FP32 tables only: species-B like-particle rows as (source local index, FP32 coefficient bits)
 };
 
 }  // namespace trbl
@@ -119,6 +120,8 @@ struct trbl_hamiltonian {
   void* garena = nullptr;
   void* gwork = nullptr;   // work items of the grouped kernel
   int rows_per_item = 0;   // neutron rows per work item (autotuned)
+  int apply_kernel = TRBL_APPLY_FAST;  // FP32 product: TRBL_APPLY_FAST where it applies, else the grouped kernel
+  int blocks_per_sm = 8;   // resident thread blocks per SM the FP32 fast kernel is compiled for (8 or 6)
   void* grad = nullptr;  // gradient tables, built on the first trbl_grad call
   size_t arena_bytes = 0;
 };
@@ -143,6 +146,17 @@ int launch_grouped_batch(const void* hs_dev, const void* gs_dev, int nset, int n
 // returns -1 (nothing launched) otherwise.
 int launch_grouped(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, int64_t ldw, int q,
                    int dtype, cudaStream_t s);
+// FP32 fast product (apply_fast.cu): enqueues W = H V and returns TRBL_OK or
+// an error, or returns -1 (nothing launched) when it does not apply (dtype,
+// q, alignment, sizes, or h->apply_kernel).
+int launch_fast(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, int64_t ldw, int q, int dtype,
+                cudaStream_t s);
+size_t fast_smem_bytes(const trbl_hamiltonian* h);
+// The fast product over nset Hamiltonians of h0's basis (device arrays of
+// DevH<float> / DevG<float>); -1 when it does not apply.
+int launch_fast_batch(const trbl_hamiltonian* h0, const void* hs_dev, const void* gs_dev, int nset, int nwork,
+                      size_t smem, const void* V, int64_t ldv, int64_t sv, void* W, int64_t ldw, int64_t sw, int q,
+                      cudaStream_t s);
 // Enqueues W = H V (apply.cu).
 int launch_apply(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, int64_t ldw,
                  int q, int dtype, cudaStream_t s);

@@ -1139,7 +1139,8 @@ struct BatchDriver {
   std::vector<cudaStream_t> ss;     // one stream per set
   std::vector<cudaEvent_t> ev_done;  // end of a set's host-driven work
   int nset = 0, nwork = 0, dtype = 0, device = 0, nthreads = 1;
-  size_t smem = 0;
+  size_t smem = 0, smem_fast = 0;
+  const trbl_hamiltonian* h0 = nullptr;  // the first set's Hamiltonian: launch shape of the batch's product
   int64_t D = 0;
   int q = 0, mb = 0;
   void* shared = nullptr;  // V_k and W of all sets, set-major
@@ -1249,7 +1250,9 @@ struct BatchDriver {
       if (hs[i]->rows_per_item != hs[0]->rows_per_item)
         TRY(set_work_items(const_cast<trbl_hamiltonian*>(hs[i]), hs[0]->rows_per_item));
       smem = std::max(smem, grouped_smem_bytes(hs[i], dtype));
+      if (dtype == TRBL_F32) smem_fast = std::max(smem_fast, fast_smem_bytes(hs[i]));
     }
+    h0 = hs[0];
     nwork = hs[0]->g32.nwork;
     TRBL_CUDA(cudaGetDevice(&device));
     nthreads = int(std::max(1u, std::min(16u, std::thread::hardware_concurrency())));
@@ -1340,8 +1343,16 @@ struct BatchDriver {
   int enqueue(bool append) {
     T* V0 = static_cast<T*>(shared);
     const size_t dq = size_t(D) * q;
-    TRY(launch_grouped_batch(tables, static_cast<char*>(tables) + sizeof(DevH<T>) * nset, nset, nwork, smem, V0, q,
-                             int64_t(dq), V0 + dq * nset, q, int64_t(dq), q, dtype, s));
+    const void* gtab = static_cast<char*>(tables) + sizeof(DevH<T>) * nset;
+    int rf = -1;
+    if (dtype == TRBL_F32)
+      rf = launch_fast_batch(h0, tables, gtab, nset, nwork, smem_fast, V0, q, int64_t(dq), V0 + dq * nset, q,
+                             int64_t(dq), q, s);
+    if (rf == -1)
+      TRY(launch_grouped_batch(tables, gtab, nset, nwork, smem, V0, q, int64_t(dq), V0 + dq * nset, q, int64_t(dq), q,
+                               dtype, s));
+    else if (rf != TRBL_OK)
+      return rf;
     const int nb = sets[0]->nb;
     const T* const* cB = P_basis;
     const T* const* cW = P_W;

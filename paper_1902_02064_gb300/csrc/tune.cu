@@ -1,16 +1,45 @@
-// Autotuner of the grouped block product: the number of neutron rows per
-// work item sets the grid size, the share of staging work per thread block
-// and how many target determinants are in flight (L2 reuse).  Each candidate
-// is timed with CUDA events on the caller's stream and the fastest is kept.
+// Autotuner of the block product's launch shape.  Three knobs:
+// * the kernel: the grouped kernel (any q, FP32 or FP64) or the FP32 fast
+//   kernel (rows of 32, 64 or 128 bytes);
+// * neutron rows per work item: the grid size, the share of staging work per
+//   thread block and how many target determinants are in flight (L2 reuse);
+// * resident thread blocks per SM the fast kernel is compiled for (8 blocks
+//   at 32 registers a thread, or 6 at 40): warps in flight against
+//   registers per warp.
+// The lanes per element and 16-byte chunks per lane follow from q and the
+// element size (one lane group reads one whole row of V).  Each candidate is
+// timed with CUDA events on the caller's stream and the fastest is kept;
+// the product's results do not depend on the choice.
 #include <algorithm>
+#include <cmath>
 
 #include "internal.h"
 
 using namespace trbl;
 
+namespace {
+
+struct Shape {
+  int kernel, rows, bps;
+};
+
+// Candidate order, as reported in trbl_apply_autotune's ms[].
+constexpr Shape kCand[TRBL_TUNE_CANDIDATES] = {
+    {TRBL_APPLY_GROUPED, 16, 8}, {TRBL_APPLY_GROUPED, 32, 8}, {TRBL_APPLY_GROUPED, 64, 8},
+    {TRBL_APPLY_GROUPED, 128, 8}, {TRBL_APPLY_FAST, 16, 8},   {TRBL_APPLY_FAST, 32, 8},
+    {TRBL_APPLY_FAST, 64, 8},     {TRBL_APPLY_FAST, 16, 6},   {TRBL_APPLY_FAST, 32, 6},
+    {TRBL_APPLY_FAST, 64, 6}};
+
+int set_shape(trbl_hamiltonian* h, const Shape& c) {
+  h->apply_kernel = c.kernel;
+  h->blocks_per_sm = c.bps;
+  return h->rows_per_item == c.rows ? TRBL_OK : set_work_items(h, c.rows);
+}
+
+}  // namespace
+
 extern "C" int trbl_apply_autotune(trbl_hamiltonian* h, int q, int dtype, float* ms, int* best_rows, void* stream) {
   clear_error();
-  static const int kCand[4] = {16, 32, 64, 128};
   if (!h) return fail(TRBL_ERR_ARG, "null Hamiltonian");
   if (q < 1 || q > 64 || (dtype != TRBL_F32 && dtype != TRBL_F64)) return fail(TRBL_ERR_ARG, "bad q or dtype");
   if (!h->garena) return fail(TRBL_ERR_ARG, "the grouped product is not available for this basis");
@@ -24,11 +53,15 @@ extern "C" int trbl_apply_autotune(trbl_hamiltonian* h, int q, int dtype, float*
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  const bool fast = dtype == TRBL_F32 && (q == 8 || q == 16 || q == 32) && h->g32.likeB && h->b->ND <= 31 &&
+                    h->b->D * q < (int64_t(1) << 31);
   float best = 1e30f;
-  int bestr = h->rows_per_item;
+  Shape keep{h->apply_kernel, h->rows_per_item, h->blocks_per_sm};
   int rc = TRBL_OK;
-  for (int c = 0; c < 4 && !rc; ++c) {
-    rc = set_work_items(h, kCand[c]);
+  for (int c = 0; c < TRBL_TUNE_CANDIDATES && !rc; ++c) {
+    if (ms) ms[c] = NAN;
+    if (kCand[c].kernel == TRBL_APPLY_FAST && !fast) continue;
+    rc = set_shape(h, kCand[c]);
     if (rc) break;
     rc = launch_apply(h, V, q, W, q, q, dtype, s);  // warm-up
     if (rc) break;
@@ -42,15 +75,15 @@ extern "C" int trbl_apply_autotune(trbl_hamiltonian* h, int q, int dtype, float*
     if (ms) ms[c] = t;
     if (t < best) {
       best = t;
-      bestr = kCand[c];
+      keep = kCand[c];
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(buf);
   if (rc) return rc;
-  if (best_rows) *best_rows = bestr;
-  return set_work_items(h, bestr);
+  if (best_rows) *best_rows = keep.rows;
+  return set_shape(h, keep);
 }
 
 extern "C" int trbl_apply_set_rows(trbl_hamiltonian* h, int rows_per_item) {
@@ -59,4 +92,23 @@ extern "C" int trbl_apply_set_rows(trbl_hamiltonian* h, int rows_per_item) {
   if (rows_per_item < 1 || rows_per_item > 4096) return fail(TRBL_ERR_ARG, "rows per work item must be in [1, 4096]");
   if (!h->garena) return fail(TRBL_ERR_ARG, "the grouped product is not available for this basis");
   return set_work_items(h, rows_per_item);
+}
+
+extern "C" int trbl_apply_set_shape(trbl_hamiltonian* h, int kernel, int rows_per_item, int blocks_per_sm) {
+  clear_error();
+  if (!h) return fail(TRBL_ERR_ARG, "null Hamiltonian");
+  if (kernel != TRBL_APPLY_GROUPED && kernel != TRBL_APPLY_FAST) return fail(TRBL_ERR_ARG, "unknown kernel %d", kernel);
+  if (rows_per_item < 1 || rows_per_item > 4096) return fail(TRBL_ERR_ARG, "rows per work item must be in [1, 4096]");
+  if (blocks_per_sm != 6 && blocks_per_sm != 8) return fail(TRBL_ERR_ARG, "blocks per SM must be 6 or 8");
+  if (!h->garena) return fail(TRBL_ERR_ARG, "the grouped product is not available for this basis");
+  return set_shape(h, Shape{kernel, rows_per_item, blocks_per_sm});
+}
+
+extern "C" int trbl_apply_get_shape(const trbl_hamiltonian* h, int* kernel, int* rows_per_item, int* blocks_per_sm) {
+  clear_error();
+  if (!h) return fail(TRBL_ERR_ARG, "null Hamiltonian");
+  if (kernel) *kernel = h->apply_kernel;
+  if (rows_per_item) *rows_per_item = h->rows_per_item;
+  if (blocks_per_sm) *blocks_per_sm = h->blocks_per_sm;
+  return TRBL_OK;
 }

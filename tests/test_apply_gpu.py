@@ -131,16 +131,20 @@ def _sample_rows(L, n_rand, seed):
     return sorted(rows)
 
 
-@pytest.mark.parametrize("name,q,dtype", [("s20_4p4n", 16, torch.float64),
-                                          ("s20_4p4n", 16, torch.float32),
-                                          ("s20_5p5n", 32, torch.float32)])
-def test_apply_full_size_sampled_rows(name, q, dtype):
+@pytest.mark.parametrize("name,q,dtype,kernel", [("s20_4p4n", 16, torch.float64, trbl.TRBL_APPLY_GROUPED),
+                                                 ("s20_4p4n", 16, torch.float32, trbl.TRBL_APPLY_FAST),
+                                                 ("s20_4p4n", 32, torch.float32, trbl.TRBL_APPLY_GROUPED),
+                                                 ("s20_5p5n", 32, torch.float32, trbl.TRBL_APPLY_FAST)])
+def test_apply_full_size_sampled_rows(name, q, dtype, kernel):
+    """Sampled rows at full size, in the launch shape the bench times for
+    the 18.6M-dim workload (fast kernel, 16 rows per work item)."""
     w, sa, sb, inter = synth.workload(name)
     L = oh.LazyIndex(sa.twom, w.nA, sb.twom, w.nB, w.twoM)
     T = oh.TermTables(inter)
     tb = trbl.Basis(sa, w.nA, sb, w.nB, w.twoM)
     assert tb.dim == L.dim
     th = trbl.Hamiltonian.from_interaction(tb, inter)
+    trbl.apply_set_shape(th, kernel, 16, 8)
     g = torch.Generator(device="cuda")
     g.manual_seed(w.seed)
     V = torch.rand((tb.dim, q), generator=g, device="cuda", dtype=dtype) * 2 - 1
@@ -168,7 +172,8 @@ def test_apply_full_size_sampled_rows(name, q, dtype):
 @pytest.mark.parametrize("kA,kB,twoM,q,dtype", [(0, 2, 0, 4, torch.float32), (2, 0, 0, 2, torch.float64),
                                                 (1, 1, 2, 8, torch.float32), (3, 2, 1, 16, torch.float64)])
 def test_apply_edge_cases_grouped_path(kA, kB, twoM, q, dtype):
-    """Row sizes that are multiples of 16 bytes take the grouped kernel."""
+    """Row sizes that are multiples of 16 bytes take the grouped kernel (FP32
+    rows of 32, 64 or 128 bytes the fast kernel)."""
     sp = synth.make_space(synth.SPACE12_SHELLS)
     inter = synth.draw_interaction(sp, sp, 33)
     B = ob.ProductBasis(sp.twom, kA, sp.twom, kB, twoM)
@@ -215,3 +220,85 @@ def test_launch_shape_does_not_change_results(medium):
     _check(outs[0].double().numpy(), H, V.cpu().double().numpy(), torch.float32)
     with pytest.raises(trbl.TrblError):
         trbl.apply_set_rows(th, 0)
+
+
+SHAPES = [(trbl.TRBL_APPLY_GROUPED, 16, 8), (trbl.TRBL_APPLY_FAST, 16, 8), (trbl.TRBL_APPLY_FAST, 64, 6),
+          (trbl.TRBL_APPLY_FAST, 1, 8), (trbl.TRBL_APPLY_FAST, 4096, 6)]
+
+
+@pytest.mark.parametrize("q", [8, 16, 32])
+def test_fast_kernel_every_element_matches_oracle(small, medium, q):
+    """The FP32 fast kernel (packed tables, 32-bit offsets, paired FMAs) and
+    the grouped kernel, each at several launch shapes, against the oracle's
+    CSR H V on every element; both kernels sum each row in the same order,
+    so their results are also bit-identical."""
+    for w, B, H, tb, th in (small, medium):
+        V = torch.from_numpy(synth.random_block(B.dim, q, 40 + q)).float()
+        Vc = V.cuda()
+        outs = []
+        for kern, rows, bps in SHAPES:
+            trbl.apply_set_shape(th, kern, rows, bps)
+            assert trbl.apply_get_shape(th) == (kern, rows, bps)
+            W = th.apply(Vc)
+            torch.cuda.synchronize()
+            _check(W.cpu().double().numpy(), H, V.double().numpy(), torch.float32)
+            outs.append(W.cpu())
+        trbl.apply_set_shape(th, trbl.TRBL_APPLY_FAST, 16, 8)
+        for o in outs[1:]:
+            assert torch.equal(o, outs[0])
+
+
+@pytest.mark.parametrize("kA,kB,twoM,q", [(0, 2, 0, 8), (2, 0, 0, 16), (1, 1, 2, 32), (3, 2, 1, 8), (4, 1, -3, 16)])
+def test_fast_kernel_edge_particle_numbers(kA, kB, twoM, q):
+    """Empty species, one particle, odd 2M: the fast kernel against the oracle."""
+    sp = synth.make_space(synth.SPACE12_SHELLS)
+    inter = synth.draw_interaction(sp, sp, 34)
+    B = ob.ProductBasis(sp.twom, kA, sp.twom, kB, twoM)
+    H = oh.assemble(B, inter)
+    tb = trbl.Basis(sp, kA, sp, kB, twoM)
+    th = trbl.Hamiltonian.from_interaction(tb, inter)
+    trbl.apply_set_shape(th, trbl.TRBL_APPLY_FAST, 16, 8)
+    V = torch.from_numpy(synth.random_block(B.dim, q, 3)).float()
+    W = th.apply(V.cuda())
+    torch.cuda.synchronize()
+    _check(W.cpu().double().numpy(), H, V.double().numpy(), torch.float32)
+
+
+def test_fast_kernel_strided_rows_and_fallback(medium):
+    """A leading dimension above q (still 16-byte rows) takes the fast kernel;
+    q = 4 (16-byte rows) falls back to the grouped kernel; both against the
+    oracle."""
+    w, B, H, tb, th = medium
+    trbl.apply_set_shape(th, trbl.TRBL_APPLY_FAST, 16, 8)
+    big = torch.from_numpy(synth.random_block(B.dim, 24, 6)).float().cuda()
+    V = big[:, 4:20]
+    Wbig = torch.full((B.dim, 20), 3.0, dtype=torch.float32, device="cuda")
+    W = Wbig[:, 4:20]
+    th.apply(V, W)
+    torch.cuda.synchronize()
+    _check(W.cpu().double().numpy(), H, V.cpu().double().numpy(), torch.float32)
+    assert torch.all(Wbig[:, :4] == 3.0)
+    V4 = torch.from_numpy(synth.random_block(B.dim, 4, 7)).float()
+    W4 = th.apply(V4.cuda())
+    torch.cuda.synchronize()
+    _check(W4.cpu().double().numpy(), H, V4.double().numpy(), torch.float32)
+
+
+def test_autotune_candidates_and_choice(medium):
+    """The autotuner times every shape that applies (NaN for the others),
+    keeps the fastest, and leaves W unchanged."""
+    w, B, H, tb, th = medium
+    V = torch.from_numpy(synth.random_block(B.dim, 32, 9)).float().cuda()
+    ref = th.apply(V).cpu()
+    ms, rows = trbl.apply_autotune(th, 32, trbl.TRBL_F32)
+    assert len(ms) == trbl.TRBL_TUNE_CANDIDATES and all(np.isfinite(ms))
+    kern, r, bps = trbl.apply_get_shape(th)
+    assert r == rows and kern in (trbl.TRBL_APPLY_GROUPED, trbl.TRBL_APPLY_FAST)
+    assert torch.equal(th.apply(V).cpu(), ref)
+    ms64, _ = trbl.apply_autotune(th, 16, trbl.TRBL_F64)
+    assert all(np.isfinite(ms64[:4])) and not any(np.isfinite(ms64[4:]))
+    with pytest.raises(trbl.TrblError):
+        trbl.apply_set_shape(th, 7, 16, 8)
+    with pytest.raises(trbl.TrblError):
+        trbl.apply_set_shape(th, trbl.TRBL_APPLY_FAST, 16, 5)
+    trbl.apply_set_shape(th, trbl.TRBL_APPLY_FAST, 16, 8)
