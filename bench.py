@@ -630,6 +630,7 @@ def run_apply_only(args):
         tune_ms, tune_rows = None, args.rows
         kern = trbl.TRBL_APPLY_GROUPED if args.kernel == "grouped" else trbl.TRBL_APPLY_FAST
         trbl.apply_set_shape(th, kern, args.rows, args.bps)
+        trbl.apply_set_compensated(th, args.comp)
     else:
         tune_ms, tune_rows = trbl.apply_autotune(th, q, trbl.TRBL_F64 if args.fp64 else trbl.TRBL_F32)
     g = torch.Generator(device="cuda")
@@ -654,6 +655,7 @@ def run_apply_only(args):
                       "ms_per_apply": ms, "gnzq_per_s": nnz * q / (ms * 1e-3) / 1e9,
                       "structural_nnz": nnz, "slab_rows_R": R, "algorithmic_bytes": b_slab,
                       "rows_per_item": tune_rows, "autotune_ms": tune_ms, "shape": trbl.apply_get_shape(th),
+                      "compensated": bool(args.comp),
                       "achieved_gbs": b_slab / (ms * 1e-3) / 1e9, "frac_of_measured_hbm": b_slab / (ms * 1e-3) / 1e9 / peak}),
           flush=True)
 
@@ -685,6 +687,8 @@ def main():
                     help="--apply-only with --rows: the product kernel")
     ap.add_argument("--bps", type=int, default=8, choices=[6, 8],
                     help="--apply-only with --rows: resident blocks per SM of the fast kernel")
+    ap.add_argument("--comp", action="store_true",
+                    help="--apply-only with --rows: compensated row sums in the fast kernel")
     ap.add_argument("--fp64", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

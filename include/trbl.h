@@ -199,9 +199,13 @@ int trbl_block_dot_tc(const void* B, int64_t ldb, int m, const void* W, int64_t 
  * leading dimensions ldi >= K and ldo >= n, dtype TRBL_F32 or TRBL_F64, must
  * not overlap; U: device FP64 K x n row-major (ld ldu >= n).  algo:
  * TRBL_PROJ_TENSOR or TRBL_PROJ_CUDA_CORE (FP32 data; FP64 data ignore it);
- * the tensor-core form needs n <= 32, In 16-byte aligned with ldi a multiple
- * of 4, and falls back to the CUDA cores otherwise.  Allocates stream-ordered
- * scratch (cudaMallocAsync) for the tensor-core form.  Asynchronous on
+ * the tensor-core form needs In 16-byte aligned with ldi a multiple of 4
+ * and falls back to the CUDA cores otherwise.  For n > 32 it is the wide
+ * form the solver uses for the thick restart v_i := sum_j v_j U_ji and the
+ * Ritz vectors (Sec. III D): 128 x 128 output tiles, split TF32 operands, a
+ * fresh tensor-memory accumulator every 32 values of K, summed in FP32
+ * registers with round-to-nearest adds.  Allocates stream-ordered scratch
+ * (cudaMallocAsync) for the tensor-core form.  Asynchronous on
  * stream.  Errors: TRBL_ERR_ARG, TRBL_ERR_OOM, TRBL_ERR_CUDA. */
 int trbl_block_update(const void* In, int64_t ldi, int K, const double* U, int64_t ldu, int n, void* Out,
                       int64_t ldo, int64_t D, double alpha, double beta, int dtype, int algo, void* stream);
@@ -349,6 +353,14 @@ int trbl_apply_set_shape(trbl_hamiltonian* h, int kernel, int rows_per_item, int
 
 /* The current launch shape (any output may be NULL).  Host only. */
 int trbl_apply_get_shape(const trbl_hamiltonian* h, int* kernel, int* rows_per_item, int* blocks_per_sm);
+
+/* Summation of the FP32 fast kernel's rows.  0 (default): one FP32 sum per
+ * column in the grouped kernel's order.  1: short FP32 partial sums (one
+ * cross-term task, or up to 8 like-particle sources) added into a two-word
+ * row sum by Knuth's TwoSum, so the rounding of a row does not grow with
+ * its length; the product's error is then set by the FP32 inputs.  Host
+ * only; not while a product of h is running.  Errors: TRBL_ERR_ARG. */
+int trbl_apply_set_compensated(trbl_hamiltonian* h, int on);
 
 /* Stepwise form of trbl_solve for callers that drive the iteration
  * themselves.  A solver owns its device workspace (basis of D x max_basis

@@ -22,6 +22,6 @@ from ._lib import (  # noqa: F401
     trbl_solver_create, trbl_solver_step, trbl_solver_step_host, trbl_solver_block,
     trbl_solver_stats, trbl_solver_destroy, trbl_solver_state_bytes, trbl_solver_save, trbl_solver_load,
     trbl_param_count, trbl_grad, arrays_from_theta, clusters_of, hf_gradient, hf_gradient_clusters, LowestEigenvalues,
-    solve_batch, apply_autotune, apply_set_rows, apply_set_shape, apply_get_shape,
+    solve_batch, apply_autotune, apply_set_rows, apply_set_shape, apply_get_shape, apply_set_compensated,
     Basis, Hamiltonian, Solver, solve,
 )

@@ -104,6 +104,7 @@ def lib():
         "trbl_apply_set_rows": (C.c_int, [_VP, C.c_int]),
         "trbl_apply_set_shape": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int]),
         "trbl_apply_get_shape": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "trbl_apply_set_compensated": (C.c_int, [_VP, C.c_int]),
         "trbl_kernel_launches": (C.c_longlong, []),
         "trbl_last_error": (C.c_char_p, []),
     }
@@ -657,6 +658,11 @@ def apply_set_rows(h: "Hamiltonian", rows_per_item: int):
 def apply_set_shape(h: "Hamiltonian", kernel: int, rows_per_item: int, blocks_per_sm: int = 8):
     """Sets the product's kernel, rows per work item and blocks per SM."""
     _check(lib().trbl_apply_set_shape(h.handle, int(kernel), int(rows_per_item), int(blocks_per_sm)))
+
+
+def apply_set_compensated(h: "Hamiltonian", on: bool):
+    """Compensated (TwoSum) row sums in the FP32 fast product on or off."""
+    _check(lib().trbl_apply_set_compensated(h.handle, 1 if on else 0))
 
 
 def apply_get_shape(h: "Hamiltonian"):

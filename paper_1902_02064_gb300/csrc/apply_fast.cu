@@ -23,6 +23,15 @@
 //   ranges of the staged proton jumps with a warp scan, the other warps
 //   stage the like-particle sources meanwhile.
 //
+// Summation: by default every product of a row goes into one FP32 sum per
+// column, in the grouped kernel's order (the two kernels agree bit for
+// bit).  With compensated sums (trbl_apply_set_compensated) a lane adds the
+// products of one cross-term task, or of at most 8 like-particle sources,
+// into a short FP32 partial sum, and the partial sums into a two-word
+// (hi + lo) row sum by Knuth's TwoSum: the rounding error of a row no longer
+// grows with its ~900 terms, so the FP32 product's error drops toward the
+// rounding of its inputs (the FP32 vector and coefficients).
+//
 // Partial sums of the lane groups are combined with warp shuffles and one
 // group stores the row: no atomics, a fixed summation order.
 #include <algorithm>
@@ -59,8 +68,50 @@ __device__ __forceinline__ void axpy4(u64 (&acc)[2], float c, u64 x0, u64 x1) {
   fma2(acc[0], cc, x0);
   fma2(acc[1], cc, x1);
 }
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+  u64 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
+  u64 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+// Row accumulator of a lane's four columns: with COMP the running sum is
+// kept as hi + lo, each partial sum t entering by Knuth's TwoSum (exact:
+// hi + lo + t = hi' + lo' up to the rounding of lo), so the rounding of a
+// long sum no longer grows with its length; without COMP a plain sum.
+template <bool COMP>
+struct RowAcc {
+  u64 hi[2] = {0ull, 0ull};
+  u64 lo[2] = {0ull, 0ull};
+  __device__ __forceinline__ void add(const u64 (&t)[2]) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      if (COMP) {
+        const u64 sum = add2(hi[i], t[i]);
+        const u64 tb = sub2(sum, hi[i]);
+        const u64 hb = sub2(sum, tb);
+        lo[i] = add2(lo[i], add2(sub2(hi[i], hb), sub2(t[i], tb)));
+        hi[i] = sum;
+      } else {
+        hi[i] = add2(hi[i], t[i]);
+      }
+    }
+  }
+  __device__ __forceinline__ void result(float (&r)[4]) const {
+    u64 s0 = hi[0], s1 = hi[1];
+    if (COMP) {
+      s0 = add2(s0, lo[0]);
+      s1 = add2(s1, lo[1]);
+    }
+    unpack2(s0, r[0], r[1]);
+    unpack2(s1, r[2], r[3]);
+  }
+};
 
-template <int LPE>
+template <int LPE, bool COMP>
 __device__ __forceinline__ void fast_body(const DevH<float>& h, const DevG<float>& g, int item_index,
                                           const float* __restrict__ V, int ld, float* __restrict__ W, int64_t ldw) {
   constexpr int G = 32 / LPE;  // element groups per warp
@@ -127,27 +178,47 @@ __device__ __forceinline__ void fast_body(const DevH<float>& h, const DevG<float
   for (int rr = warp; rr < nrows; rr += kWarps) {
     const int iB = r0 + rr;
     const int pB = gB0 + iB;
+    // With COMP, partial sums of at most 8 like-particle elements (or of
+    // one task of the cross term) enter a compensated row accumulator one at a
+    // time; without it every product goes straight into one FP32 sum, in the
+    // grouped kernel's order.
+    RowAcc<COMP> racc;
     u64 acc[2] = {0ull, 0ull};
+    constexpr int kStep = COMP ? 8 * G : (1 << 28);  // one pass without COMP
     // like-particle rows of species B: sources (pA', nB) in the target's own slab
     {
-      const int e1 = h.hoffB[pB + 1];
+      const int e0 = h.hoffB[pB], e1 = h.hoffB[pB + 1];
+      for (int c0 = e0 + grp; c0 < e1; c0 += kStep) {
+        const int ce = COMP ? min(e1, c0 + kStep) : e1;
 #pragma unroll 2
-      for (int e = h.hoffB[pB] + grp; e < e1; e += G) {
-        const int2 u = g.likeB[e];
-        u64 x0, x1;
-        ldg16(Vnn + u.x * ld, x0, x1);
-        axpy4(acc, __int_as_float(u.y), x0, x1);
+        for (int e = c0; e < ce; e += G) {
+          const int2 u = g.likeB[e];
+          u64 x0, x1;
+          ldg16(Vnn + u.x * ld, x0, x1);
+          axpy4(acc, __int_as_float(u.y), x0, x1);
+        }
+        if (COMP) {
+          racc.add(acc);
+          acc[0] = acc[1] = 0ull;
+        }
       }
     }
     // like-particle rows of species A: sources (pA, nB')
     {
       const float* Vpp = Vl + iB * ld;
+      for (int c0 = grp; c0 < Q; c0 += kStep) {
+        const int ce = COMP ? min(Q, c0 + kStep) : Q;
 #pragma unroll 2
-      for (int i = grp; i < Q; i += G) {
-        const int2 u = pp[i];
-        u64 x0, x1;
-        ldg16(Vpp + u.x, x0, x1);
-        axpy4(acc, __int_as_float(u.y), x0, x1);
+        for (int i = c0; i < ce; i += G) {
+          const int2 u = pp[i];
+          u64 x0, x1;
+          ldg16(Vpp + u.x, x0, x1);
+          axpy4(acc, __int_as_float(u.y), x0, x1);
+        }
+        if (COMP) {
+          racc.add(acc);
+          acc[0] = acc[1] = 0ull;
+        }
       }
     }
     // proton jump x neutron jump of opposite 2m transfer: one task per
@@ -179,11 +250,15 @@ __device__ __forceinline__ void fast_body(const DevH<float>& h, const DevG<float
           ldg16(nsrc + pj[p], a0, a1);
           axpy4(acc, c0, a0, a1);
         }
+        if (COMP) {
+          racc.add(acc);
+          acc[0] = acc[1] = 0ull;
+        }
       }
     }
+    if (!COMP) racc.add(acc);
     float r[4];
-    unpack2(acc[0], r[0], r[1]);
-    unpack2(acc[1], r[2], r[3]);
+    racc.result(r);
 #pragma unroll
     for (int o = LPE; o < 32; o <<= 1)
 #pragma unroll
@@ -193,52 +268,52 @@ __device__ __forceinline__ void fast_body(const DevH<float>& h, const DevG<float
   }
 }
 
-template <int LPE, int MINB>
+template <int LPE, int MINB, bool COMP>
 __global__ void __launch_bounds__(kThreads, MINB)
     apply_fast_kernel(DevH<float> h, DevG<float> g, const float* __restrict__ V, int ld, float* __restrict__ W,
                       int64_t ldw) {
-  fast_body<LPE>(h, g, blockIdx.x, V, ld, W, ldw);
+  fast_body<LPE, COMP>(h, g, blockIdx.x, V, ld, W, ldw);
 }
 
 // Several Hamiltonians on one basis: blockIdx.y selects the set; set s reads
 // V + s * sv and writes W + s * sw.
-template <int LPE, int MINB>
+template <int LPE, int MINB, bool COMP>
 __global__ void __launch_bounds__(kThreads, MINB)
     apply_fast_batch_kernel(const DevH<float>* __restrict__ hs, const DevG<float>* __restrict__ gs,
                             const float* __restrict__ V, int ld, int64_t sv, float* __restrict__ W, int64_t ldw,
                             int64_t sw) {
   const DevH<float> h = hs[blockIdx.y];
   const DevG<float> g = gs[blockIdx.y];
-  fast_body<LPE>(h, g, blockIdx.x, V + blockIdx.y * sv, ld, W + blockIdx.y * sw, ldw);
+  fast_body<LPE, COMP>(h, g, blockIdx.x, V + blockIdx.y * sv, ld, W + blockIdx.y * sw, ldw);
 }
 
 size_t fast_smem(const DevG<float>& g) {
   return size_t(g.maxQ) * 8 + size_t(g.maxP + 1) * 4 + size_t(g.maxP + 1) * g.maxK * 4 + 33 * 4;
 }
 
-template <int LPE, int MINB>
+template <int LPE, int MINB, bool COMP>
 int launch_lpe(const DevH<float>& h, const DevG<float>& g, const float* V, int ld, float* W, int64_t ldw,
                cudaStream_t s) {
-  static const cudaError_t cfg =
-      cudaFuncSetAttribute(apply_fast_kernel<LPE, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+  static const cudaError_t cfg = cudaFuncSetAttribute(apply_fast_kernel<LPE, MINB, COMP>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
   TRBL_CUDA(cfg);
   const size_t sm = fast_smem(g);
   if (sm > size_t(kMaxSmem)) return fail(TRBL_ERR_ARG, "product needs %zu bytes of shared memory", sm);
-  apply_fast_kernel<LPE, MINB><<<g.nwork, kThreads, sm, s>>>(h, g, V, ld, W, ldw);
+  apply_fast_kernel<LPE, MINB, COMP><<<g.nwork, kThreads, sm, s>>>(h, g, V, ld, W, ldw);
   note_launch();
   TRBL_CUDA(cudaGetLastError());
   return TRBL_OK;
 }
 
-template <int LPE, int MINB>
+template <int LPE, int MINB, bool COMP>
 int launch_batch_lpe(const DevH<float>* hs, const DevG<float>* gs, int nset, int nwork, size_t sm, const float* V,
                      int ld, int64_t sv, float* W, int64_t ldw, int64_t sw, cudaStream_t s) {
-  static const cudaError_t cfg = cudaFuncSetAttribute(apply_fast_batch_kernel<LPE, MINB>,
+  static const cudaError_t cfg = cudaFuncSetAttribute(apply_fast_batch_kernel<LPE, MINB, COMP>,
                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
   TRBL_CUDA(cfg);
   if (sm > size_t(kMaxSmem)) return fail(TRBL_ERR_ARG, "product needs %zu bytes of shared memory", sm);
   const dim3 grid{static_cast<unsigned>(nwork), static_cast<unsigned>(nset), 1u};
-  apply_fast_batch_kernel<LPE, MINB><<<grid, kThreads, sm, s>>>(hs, gs, V, ld, sv, W, ldw, sw);
+  apply_fast_batch_kernel<LPE, MINB, COMP><<<grid, kThreads, sm, s>>>(hs, gs, V, ld, sv, W, ldw, sw);
   note_launch();
   TRBL_CUDA(cudaGetLastError());
   return TRBL_OK;
@@ -255,6 +330,28 @@ bool fast_ok(const trbl_hamiltonian* h, const void* V, int64_t ldv, const void* 
   return true;
 }
 
+template <int LPE>
+int launch_q(const trbl_hamiltonian* h, const float* v, int ld, float* w, int64_t ldw, cudaStream_t s) {
+  const bool b6 = h->blocks_per_sm == 6;
+  if (h->apply_compensated)
+    return b6 ? launch_lpe<LPE, 6, true>(h->d32, h->g32, v, ld, w, ldw, s)
+              : launch_lpe<LPE, 8, true>(h->d32, h->g32, v, ld, w, ldw, s);
+  return b6 ? launch_lpe<LPE, 6, false>(h->d32, h->g32, v, ld, w, ldw, s)
+            : launch_lpe<LPE, 8, false>(h->d32, h->g32, v, ld, w, ldw, s);
+}
+
+template <int LPE>
+int launch_batch_q(const trbl_hamiltonian* h0, const DevH<float>* hs, const DevG<float>* gs, int nset, int nwork,
+                   size_t smem, const float* v, int ld, int64_t sv, float* w, int64_t ldw, int64_t sw,
+                   cudaStream_t s) {
+  const bool b6 = h0->blocks_per_sm == 6;
+  if (h0->apply_compensated)
+    return b6 ? launch_batch_lpe<LPE, 6, true>(hs, gs, nset, nwork, smem, v, ld, sv, w, ldw, sw, s)
+              : launch_batch_lpe<LPE, 8, true>(hs, gs, nset, nwork, smem, v, ld, sv, w, ldw, sw, s);
+  return b6 ? launch_batch_lpe<LPE, 6, false>(hs, gs, nset, nwork, smem, v, ld, sv, w, ldw, sw, s)
+            : launch_batch_lpe<LPE, 8, false>(hs, gs, nset, nwork, smem, v, ld, sv, w, ldw, sw, s);
+}
+
 }  // namespace
 
 int launch_fast(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, int64_t ldw, int q, int dtype,
@@ -263,11 +360,10 @@ int launch_fast(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, 
   const float* v = static_cast<const float*>(V);
   float* w = static_cast<float*>(W);
   const int ld = int(ldv);
-  const bool b6 = h->blocks_per_sm == 6;
   switch (q) {
-    case 8: return b6 ? launch_lpe<2, 6>(h->d32, h->g32, v, ld, w, ldw, s) : launch_lpe<2, 8>(h->d32, h->g32, v, ld, w, ldw, s);
-    case 16: return b6 ? launch_lpe<4, 6>(h->d32, h->g32, v, ld, w, ldw, s) : launch_lpe<4, 8>(h->d32, h->g32, v, ld, w, ldw, s);
-    default: return b6 ? launch_lpe<8, 6>(h->d32, h->g32, v, ld, w, ldw, s) : launch_lpe<8, 8>(h->d32, h->g32, v, ld, w, ldw, s);
+    case 8: return launch_q<2>(h, v, ld, w, ldw, s);
+    case 16: return launch_q<4>(h, v, ld, w, ldw, s);
+    default: return launch_q<8>(h, v, ld, w, ldw, s);
   }
 }
 
@@ -278,23 +374,15 @@ int launch_fast_batch(const trbl_hamiltonian* h0, const void* hs_dev, const void
                       cudaStream_t s) {
   if (h0->apply_kernel != TRBL_APPLY_FAST || !fast_ok(h0, V, ldv, W, ldw, q)) return -1;
   if ((sv | sw) % 4) return -1;
-  if (h0->b->D * ldv + (nset - 1) * sv >= (int64_t(1) << 40)) return -1;
   const auto* hs = static_cast<const DevH<float>*>(hs_dev);
   const auto* gs = static_cast<const DevG<float>*>(gs_dev);
   const float* v = static_cast<const float*>(V);
   float* w = static_cast<float*>(W);
   const int ld = int(ldv);
-  const bool b6 = h0->blocks_per_sm == 6;
   switch (q) {
-    case 8:
-      return b6 ? launch_batch_lpe<2, 6>(hs, gs, nset, nwork, smem, v, ld, sv, w, ldw, sw, s)
-                : launch_batch_lpe<2, 8>(hs, gs, nset, nwork, smem, v, ld, sv, w, ldw, sw, s);
-    case 16:
-      return b6 ? launch_batch_lpe<4, 6>(hs, gs, nset, nwork, smem, v, ld, sv, w, ldw, sw, s)
-                : launch_batch_lpe<4, 8>(hs, gs, nset, nwork, smem, v, ld, sv, w, ldw, sw, s);
-    default:
-      return b6 ? launch_batch_lpe<8, 6>(hs, gs, nset, nwork, smem, v, ld, sv, w, ldw, sw, s)
-                : launch_batch_lpe<8, 8>(hs, gs, nset, nwork, smem, v, ld, sv, w, ldw, sw, s);
+    case 8: return launch_batch_q<2>(h0, hs, gs, nset, nwork, smem, v, ld, sv, w, ldw, sw, s);
+    case 16: return launch_batch_q<4>(h0, hs, gs, nset, nwork, smem, v, ld, sv, w, ldw, sw, s);
+    default: return launch_batch_q<8>(h0, hs, gs, nset, nwork, smem, v, ld, sv, w, ldw, sw, s);
   }
 }
 

@@ -68,6 +68,20 @@ int rowgemm_tc(const float* In, int64_t ldi, int K, const double* U, int64_t ldu
 // Enqueues a copy of the tensor-core kernels' wait-timeout word to host memory.
 int tc_error_to_host(int* host, cudaStream_t s);
 
+// Wide FP32 GEMM on the tensor cores (gemm_wide_tc.cu): Out[:, 0:n] =
+// alpha In[:, 0:K] U + beta Out, U FP64 K x n row-major, any n.  The split
+// of U into the workspace (gemm_wide_tc_workspace_bytes) can be done once
+// and reused by several runs over row panels.  -1 when shapes, alignment or
+// workspace do not allow it.
+size_t gemm_wide_tc_workspace_bytes(int K, int n);
+int gemm_wide_tc_split(const double* U, int64_t ldu, int K, int n, float* ut, size_t ut_bytes, cudaStream_t s);
+int gemm_wide_tc_run(const float* In, int64_t ldi, int K, int n, const float* ut, float* Out, int64_t ldo, int64_t D,
+                     double alpha, double beta, int sm_count, cudaStream_t s);
+int gemm_wide_tc(const float* In, int64_t ldi, int K, const double* U, int64_t ldu, int n, float* Out, int64_t ldo,
+                 int64_t D, double alpha, double beta, float* ut, size_t ut_bytes, int sm_count, cudaStream_t s);
+// Enqueues a copy of the wide GEMM's wait-timeout word to host memory.
+int wide_error_to_host(int* host, cudaStream_t s);
+
 // Batched forms for nset problems of equal shapes, one launch each (plus the
 // reduction): problem s reads and writes through the s-th entry of device
 // arrays of pointers.  block_dot_batched uses about 1,024 rows per thread

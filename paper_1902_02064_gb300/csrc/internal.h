@@ -122,6 +122,7 @@ struct trbl_hamiltonian {
   int rows_per_item = 0;   // neutron rows per work item (autotuned)
   int apply_kernel = TRBL_APPLY_FAST;  // FP32 product: TRBL_APPLY_FAST where it applies, else the grouped kernel
   int blocks_per_sm = 8;   // resident thread blocks per SM the FP32 fast kernel is compiled for (8 or 6)
+  int apply_compensated = 0;  // FP32 fast kernel: compensated (TwoSum) row sums
   void* grad = nullptr;  // gradient tables, built on the first trbl_grad call
   size_t arena_bytes = 0;
 };

@@ -101,6 +101,24 @@ extern "C" int trbl_block_update(const void* In, int64_t ldi, int K, const doubl
   if (algo == TRBL_PROJ_CUDA_CORE)
     return rowgemm<float>(static_cast<const float*>(In), ldi, K, U, ldu, n, static_cast<float*>(Out), ldo, D, alpha,
                           beta, s);
+  if (n > 32) {
+    // wide update on the tensor cores (gemm_wide_tc), CUDA cores where its shapes do not apply
+    const size_t ub = gemm_wide_tc_workspace_bytes(K, n);
+    void* ut = nullptr;
+    TRBL_CUDA(cudaMallocAsync(&ut, ub, s));
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    rc = gemm_wide_tc(static_cast<const float*>(In), ldi, K, U, ldu, n, static_cast<float*>(Out), ldo, D, alpha, beta,
+                      static_cast<float*>(ut), ub, sms, s);
+    if (rc == -1)
+      rc = rowgemm<float>(static_cast<const float*>(In), ldi, K, U, ldu, n, static_cast<float*>(Out), ldo, D, alpha,
+                          beta, s);
+    cudaError_t e = cudaFreeAsync(ut, s);
+    if (rc) return rc;
+    TRBL_CUDA(e);
+    return TRBL_OK;
+  }
   Workspace ws;
   ws.tensor = true;
   ws.ut_bytes = rowgemm_tc_workspace_bytes(K);

@@ -20,7 +20,6 @@
 // threshold (an exhausted Krylov direction) is replaced by a fresh seeded
 // random vector, the block is re-orthogonalised, and beta_k = V_{k+1}^T W.
 // The small symmetric eigenproblem uses cuSOLVER's syevd (FP64).
-#include <cublas_v2.h>
 #include <cusolverDn.h>
 
 #include <algorithm>
@@ -433,9 +432,8 @@ struct Solver {
   int lwork;
   int64_t nchunk_res;
   cusolverDnHandle_t sol = nullptr;
-  cublasHandle_t blas = nullptr;
-  float* Uf = nullptr;       // FP32 copy of a small coefficient matrix for cuBLAS
-  bool emulated_ok = true;   // FP32-accurate BF16-split tensor-core GEMM available
+  float* utw = nullptr;      // split TF32 transpose of a restart / Ritz coefficient matrix (gemm_wide_tc)
+  size_t utw_bytes = 0;
   double *hbuf;  // pinned: theta[mb], res[mb], flags as doubles
   int* hflags;
   uint64_t reseed = 0;
@@ -446,7 +444,6 @@ struct Solver {
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     if (sol) cusolverDnDestroy(sol);
-    if (blas) cublasDestroy(blas);
     if (hbuf) cudaFreeHost(hbuf);
     if (syev_work) cudaFree(syev_work);
   }
@@ -494,12 +491,13 @@ struct Solver {
     TRY(tma_error_to_host(hflags + kTmaErr, s));
     TRY(dot_error_to_host(hflags + kTmaErr + 1, s));
     TRY(tc_error_to_host(hflags + kTmaErr + 2, s));
+    TRY(wide_error_to_host(hflags + kTmaErr + 3, s));
     return TRBL_OK;
   }
 
   // After the stream synchronised past cholqr2_async.
   int wait_errors() {
-    if (hflags[kTmaErr] || hflags[kTmaErr + 1] || hflags[kTmaErr + 2])
+    if (hflags[kTmaErr] || hflags[kTmaErr + 1] || hflags[kTmaErr + 2] || hflags[kTmaErr + 3])
       return fail(TRBL_ERR_CUDA, "a bounded wait in a projection kernel timed out");
     return TRBL_OK;
   }
@@ -591,58 +589,36 @@ struct Solver {
 
   // Out[rows x n] (row-major, ld ldo) = In[rows x K] (row-major, ld ldi) U,
   // U FP64 K x n row-major (ld n): the dense GEMMs of the restart and of the
-  // Ritz vectors.  Large FP32 ones (over 2e10 flops) run as cuBLAS GEMMs with
-  // the library's FP32-accurate tensor-core emulation (operands split into
-  // three BF16 parts) where it is offered, plain FP32 otherwise; FP64 data and
-  // small products use rowgemm (cuBLAS's set-up costs more than it saves
-  // there, and FP64 GEMMs run at the same FP64 rate either way).
-  int gemm_rm(const T* In, int64_t ldi, int K, const double* U, int n, T* Out, int64_t ldo, int64_t rows) {
+  // Ritz vectors.  FP32 data with n > 32 run on the tensor cores
+  // (gemm_wide_tc: split TF32, fresh accumulators every 32 K values summed
+  // in FP32 registers); FP64 data and narrow products use rowgemm.  With
+  // presplit set, utw already holds U's split (gemm_wide_tc_split).
+  int gemm_rm(const T* In, int64_t ldi, int K, const double* U, int n, T* Out, int64_t ldo, int64_t rows,
+              bool presplit = false) {
     if (rows <= 0 || n <= 0 || K <= 0) return TRBL_OK;
-    const double flops = 2.0 * double(rows) * K * n;
-    if (std::is_same<T, double>::value || flops < 2e10 || rows > INT32_MAX || ldi > INT32_MAX || ldo > INT32_MAX)
-      return rowgemm<T>(In, ldi, K, U, n, n, Out, ldo, rows, 1.0, 0.0, s);
-    if (!blas) {
-      if (cublasCreate(&blas) != CUBLAS_STATUS_SUCCESS) return fail(TRBL_ERR_CUDA, "cublasCreate failed");
-      if (cublasSetStream(blas, s) != CUBLAS_STATUS_SUCCESS) return fail(TRBL_ERR_CUDA, "cublasSetStream failed");
-    }
-    cublasStatus_t st;
-    {
-      // The library's tensor-core GEMMs need the output width to be a
-      // multiple of 8 (406 columns ran 2.4x slower than 408): pad U with zero
-      // columns when the output has room for them.
-      const int n8 = (n + 7) / 8 * 8;
-      const int M = ldo >= n8 ? n8 : n;
-      const int ldu = n8;
-      if (M != n) TRBL_CUDA(cudaMemsetAsync(Uf, 0, sizeof(float) * size_t(K) * ldu, s));
-      TRY(copy_cols<double, float>(U, n, Uf, ldu, K, n, s));
-      const float one = 1.f, zero = 0.f;
-      st = CUBLAS_STATUS_NOT_SUPPORTED;
-      if (emulated_ok) {
-        st = cublasGemmEx(blas, CUBLAS_OP_N, CUBLAS_OP_N, M, int(rows), K, &one, Uf, CUDA_R_32F, ldu, In, CUDA_R_32F,
-                          int(ldi), &zero, Out, CUDA_R_32F, int(ldo), CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
-                          CUBLAS_GEMM_DEFAULT);
-        if (st == CUBLAS_STATUS_NOT_SUPPORTED) emulated_ok = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (n > 32) {
+        int rc = presplit ? TRBL_OK : gemm_wide_tc_split(U, n, K, n, utw, utw_bytes, s);
+        if (rc == TRBL_OK) rc = gemm_wide_tc_run(In, ldi, K, n, utw, Out, ldo, rows, 1.0, 0.0, ws.sm_count, s);
+        if (rc != -1) return rc;
       }
-      if (!emulated_ok)
-        st = cublasGemmEx(blas, CUBLAS_OP_N, CUBLAS_OP_N, M, int(rows), K, &one, Uf, CUDA_R_32F, ldu, In, CUDA_R_32F,
-                          int(ldi), &zero, Out, CUDA_R_32F, int(ldo), CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
     }
-    if (st != CUBLAS_STATUS_SUCCESS) return fail(TRBL_ERR_CUDA, "cuBLAS GEMM failed (status %d)", int(st));
-    trace("restart GEMM %d (padded to a multiple of 8 where the output allows) x %lld x %d via cuBLAS (%s)", n,
-          (long long)rows, K,
-          emulated_ok ? "FP32 emulated with BF16 parts" : "FP32");
-    return TRBL_OK;
+    return rowgemm<T>(In, ldi, K, U, n, n, Out, ldo, rows, 1.0, 0.0, s);
   }
 
   // basis[:, 0:n_out] <- basis[:, 0:nb] U[:, 0:n_out] in row panels
   int compress(int nb, int n_out) {
     transpose_kernel<<<(nb * n_out + 255) / 256, 256, 0, s>>>(Aw, mb, nb, n_out, Ut); note_launch();
     TRBL_CUDA(cudaGetLastError());
+    bool presplit = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (n_out > 32) presplit = gemm_wide_tc_split(Ut, n_out, nb, n_out, utw, utw_bytes, s) == TRBL_OK;
+    }
     for (int64_t r0 = 0; r0 < D; r0 += panel_rows) {
       const int64_t nr = std::min(panel_rows, D - r0);
-      // panel rows padded to a multiple of 8 columns (see gemm_rm)
+      // panel rows padded to a multiple of 8 columns (16-byte aligned rows)
       const int ldp = (n_out + 7) / 8 * 8;
-      TRY(gemm_rm(basis + r0 * mb, mb, nb, Ut, n_out, panel, ldp, nr));
+      TRY(gemm_rm(basis + r0 * mb, mb, nb, Ut, n_out, panel, ldp, nr, presplit));
       TRY(copy_cols<T, T>(panel, ldp, basis + r0 * mb, mb, nr, n_out, s));
     }
     return TRBL_OK;
@@ -1016,7 +992,8 @@ struct Solver {
       Tm = ar.take<double>(size_t(mb) * mb);
       Aw = ar.take<double>(size_t(mb) * mb);
       Ut = ar.take<double>(size_t(mb) * mb);
-      Uf = ar.take<float>(size_t(mb) * ((mb + 7) / 8 * 8));
+      utw_bytes = std::is_same<T, float>::value ? gemm_wide_tc_workspace_bytes(mb, mb) : 0;
+      utw = ar.take<float>(utw_bytes / sizeof(float) + 4);
       theta = ar.take<double>(mb);
       res = ar.take<double>(mb);
       Xd = ar.take<double>(dq);
@@ -1160,7 +1137,7 @@ struct BatchDriver {
   SetPtrs<T>* dsp = nullptr;
   int* dcounts = nullptr;
   SetPtrs<T>* hsp = nullptr;  // pinned: the records, thresholds refreshed before each step
-  int* hcounts = nullptr;     // pinned: 2 counts per set, then the three wait-timeout words
+  int* hcounts = nullptr;     // pinned: 2 counts per set, then the four wait-timeout words
   size_t part_bytes = 0;
   std::map<int, cudaGraphExec_t> graphs;
   std::vector<int> rc;
@@ -1303,7 +1280,7 @@ struct BatchDriver {
     const size_t bytes = np * (4 * sizeof(T*) + 6 * sizeof(double*)) + np * sizeof(SetPtrs<T>) + 2 * np * sizeof(int) + 256;
     TRBL_CUDA(cudaMalloc(&bptr, bytes));
     TRBL_CUDA(cudaMallocHost(&hsp, np * sizeof(SetPtrs<T>)));
-    TRBL_CUDA(cudaMallocHost(&hcounts, (2 * np + 3) * sizeof(int)));
+    TRBL_CUDA(cudaMallocHost(&hcounts, (2 * np + 4) * sizeof(int)));
     std::vector<char> host(bytes);
     size_t off = 0;
     auto place = [&](auto** dev, auto f) {
@@ -1380,6 +1357,7 @@ struct BatchDriver {
     TRY(tma_error_to_host(hcounts + 2 * nset, s));
     TRY(dot_error_to_host(hcounts + 2 * nset + 1, s));
     TRY(tc_error_to_host(hcounts + 2 * nset + 2, s));
+    TRY(wide_error_to_host(hcounts + 2 * nset + 3, s));
     return TRBL_OK;
   }
 
@@ -1441,7 +1419,7 @@ struct BatchDriver {
         int* hf = sets[i]->hflags;
         hf[kF1] = hcounts[2 * i];
         hf[kF2] = hcounts[2 * i + 1];
-        for (int k = 0; k < 3; ++k) hf[kTmaErr + k] = hcounts[2 * nset + k];
+        for (int k = 0; k < 4; ++k) hf[kTmaErr + k] = hcounts[2 * nset + k];
       }
       const double t_step = ms_since(t0);
       ms_steps += t_step;

@@ -112,3 +112,11 @@ extern "C" int trbl_apply_get_shape(const trbl_hamiltonian* h, int* kernel, int*
   if (blocks_per_sm) *blocks_per_sm = h->blocks_per_sm;
   return TRBL_OK;
 }
+
+extern "C" int trbl_apply_set_compensated(trbl_hamiltonian* h, int on) {
+  clear_error();
+  if (!h) return fail(TRBL_ERR_ARG, "null Hamiltonian");
+  if (on != 0 && on != 1) return fail(TRBL_ERR_ARG, "compensated must be 0 or 1");
+  h->apply_compensated = on;
+  return TRBL_OK;
+}

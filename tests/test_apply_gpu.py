@@ -230,8 +230,9 @@ SHAPES = [(trbl.TRBL_APPLY_GROUPED, 16, 8), (trbl.TRBL_APPLY_FAST, 16, 8), (trbl
 def test_fast_kernel_every_element_matches_oracle(small, medium, q):
     """The FP32 fast kernel (packed tables, 32-bit offsets, paired FMAs) and
     the grouped kernel, each at several launch shapes, against the oracle's
-    CSR H V on every element; both kernels sum each row in the same order,
-    so their results are also bit-identical."""
+    CSR H V on every element; with plain sums both kernels sum each row in
+    the same order, so their results are also bit-identical.  The same with
+    compensated sums (fast kernel only), each shape against the oracle."""
     for w, B, H, tb, th in (small, medium):
         V = torch.from_numpy(synth.random_block(B.dim, q, 40 + q)).float()
         Vc = V.cuda()
@@ -246,6 +247,14 @@ def test_fast_kernel_every_element_matches_oracle(small, medium, q):
         trbl.apply_set_shape(th, trbl.TRBL_APPLY_FAST, 16, 8)
         for o in outs[1:]:
             assert torch.equal(o, outs[0])
+        trbl.apply_set_compensated(th, True)
+        for kern, rows, bps in SHAPES[1:]:
+            trbl.apply_set_shape(th, kern, rows, bps)
+            W = th.apply(Vc)
+            torch.cuda.synchronize()
+            _check(W.cpu().double().numpy(), H, V.double().numpy(), torch.float32)
+        trbl.apply_set_compensated(th, False)
+        trbl.apply_set_shape(th, trbl.TRBL_APPLY_FAST, 16, 8)
 
 
 @pytest.mark.parametrize("kA,kB,twoM,q", [(0, 2, 0, 8), (2, 0, 0, 16), (1, 1, 2, 32), (3, 2, 1, 8), (4, 1, -3, 16)])
@@ -302,3 +311,28 @@ def test_autotune_candidates_and_choice(medium):
     with pytest.raises(trbl.TrblError):
         trbl.apply_set_shape(th, trbl.TRBL_APPLY_FAST, 16, 5)
     trbl.apply_set_shape(th, trbl.TRBL_APPLY_FAST, 16, 8)
+
+
+def test_compensated_sums_match_oracle_and_cut_rounding(medium):
+    """Compensated row sums (TwoSum of short partial sums) against the
+    oracle's FP64 H V: within the FP32 bound, and with a smaller maximum
+    error than the plain FP32 sums on the same inputs."""
+    w, B, H, tb, th = medium
+    V = torch.from_numpy(synth.random_block(B.dim, 32, 12)).float()
+    Vd = V.double().numpy()
+    ref = H @ Vd
+    bound = abs(H) @ np.abs(Vd)
+    errs = {}
+    for comp in (False, True):
+        trbl.apply_set_shape(th, trbl.TRBL_APPLY_FAST, 16, 8)
+        trbl.apply_set_compensated(th, comp)
+        W = th.apply(V.cuda()).cpu().double().numpy()
+        _check(W, H, Vd, torch.float32)
+        errs[comp] = float((np.abs(W - ref) / (bound + 1e-300)).max())
+        # the launch shape does not change the compensated result either
+        trbl.apply_set_shape(th, trbl.TRBL_APPLY_FAST, 64, 6)
+        assert np.array_equal(th.apply(V.cuda()).cpu().double().numpy(), W)
+    trbl.apply_set_compensated(th, False)
+    trbl.apply_set_shape(th, trbl.TRBL_APPLY_FAST, 16, 8)
+    print("max |W - HV| / (|H||V|): plain %.2e compensated %.2e" % (errs[False], errs[True]))
+    assert errs[True] < errs[False]

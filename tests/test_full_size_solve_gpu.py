@@ -37,7 +37,11 @@ N_ROWS = 400
 # name, precision, nev, q, max_basis, tol
 CASES = [("s20_4p4n", trbl.TRBL_PREC_MIXED, 10, 16, 128, 1e-6),
          ("s20_4p4n", trbl.TRBL_PREC_F64, 3, 4, 64, 1e-9),
-         ("s20_5p5n", trbl.TRBL_PREC_MIXED, 4, 8, 96, 1e-6)]
+         ("s20_5p5n", trbl.TRBL_PREC_MIXED, 4, 8, 96, 1e-6),
+         # the headline solve of the 48Cr-sized space: 200 pairs, block 16,
+         # basis 1024 (several thick restarts, the tensor-core update for
+         # K >= 256 and the wide restart GEMM all run)
+         ("s20_4p4n", trbl.TRBL_PREC_MIXED, 200, 16, 1024, 1e-6)]
 
 _EVALS = {}
 
@@ -99,7 +103,8 @@ def test_sampled_residual_pin_detects_a_wrong_hamiltonian():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("case", CASES, ids=["s20_4p4n-mixed", "s20_4p4n-f64", "s20_5p5n-mixed"])
+@pytest.mark.parametrize("case", CASES, ids=["s20_4p4n-mixed", "s20_4p4n-f64", "s20_5p5n-mixed",
+                                             "s20_4p4n-mixed-nev200-basis1024"])
 def test_full_size_eigenpairs_pinned_by_oracle_rows(case):
     name, precision, nev, q, mb, tol = case
     w, sa, sb, inter = synth.workload(name)
@@ -108,6 +113,8 @@ def test_full_size_eigenpairs_pinned_by_oracle_rows(case):
     ev, resid, X, st = trbl.solve(th, nev, q, mb, tol, precision=precision, max_iter=1000)
     print(name, precision, st, resid / st["normH"])
     normH = st["normH"]
+    if mb == 1024:
+        assert st["restarts"] >= 3
     c = 2 if precision == trbl.TRBL_PREC_F64 else 5
     assert st["converged"] >= nev
     assert np.all(np.diff(ev) >= 0)

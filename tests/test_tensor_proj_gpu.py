@@ -160,3 +160,40 @@ def test_mixed_solver_on_both_projection_paths(projections):
     ref = np.array(gold["evals"][:40])
     assert np.abs(ev - ref).max() <= 1e-6 * normH
     assert rs.max() <= 1e-4 * normH
+
+
+@pytest.mark.parametrize("D,K,n,beta", [(1000, 7, 33, 0.0), (33333, 130, 129, 0.0), (70001, 64, 256, 0.5),
+                                        (200001, 1024, 631, 0.0), (129, 1024, 500, -1.0)])
+def test_wide_update_matches_numpy(D, K, n, beta):
+    """The wide tensor-core GEMM (thick restart and Ritz vectors, n > 32)
+    against numpy in FP64: ragged row and column tiles, K not a multiple of
+    32, the restart's shape (K = 1024, n = 631) and a beta term."""
+    In = _f32(synth.random_block(D, K, 31))
+    U = synth.random_block(K, n, 32) / np.sqrt(K)
+    O0 = _f32(synth.random_block(D, n, 33))
+    Out = _dev_ld4(O0)
+    trbl.block_update(_dev_ld4(In), torch.from_numpy(U).cuda(), Out, 1.0, beta, algo=trbl.TRBL_PROJ_TENSOR)
+    Ind, O0d = In.double().numpy(), O0.double().numpy()
+    ref = Ind @ U + beta * O0d
+    bound = np.abs(Ind) @ np.abs(U) + abs(beta) * np.abs(O0d)
+    err = np.abs(Out.cpu().double().numpy() - ref)
+    assert np.all(err <= RTOL * bound), float((err / bound).max())
+    # typical error near FP32 rounding, far inside the bound
+    assert float(np.median(err / bound)) < 1e-6
+
+
+def test_wide_update_is_unbiased():
+    """Rotating orthonormal columns by an orthogonal matrix keeps unit norms:
+    the tensor cores' round-toward-zero accumulation, left unchecked over
+    K = 1024, would shrink every norm by about 1e-5; with fresh accumulators
+    every 32 values of K the mean deviation stays at FP32 rounding level."""
+    D, K, n = 60001, 1024, 200
+    Q, _ = np.linalg.qr(synth.random_block(D, K, 41))
+    Uo, _ = np.linalg.qr(synth.random_block(K, K, 42))
+    In = _dev_ld4(_f32(Q))
+    Out = torch.zeros((D, n), dtype=torch.float32, device="cuda")
+    trbl.block_update(In, torch.from_numpy(np.ascontiguousarray(Uo[:, :n])).cuda(), Out, 1.0, 0.0,
+                      algo=trbl.TRBL_PROJ_TENSOR)
+    nrm2 = (Out.double() ** 2).sum(0).cpu().numpy()
+    assert abs(float(np.mean(nrm2 - 1.0))) < 5e-7, float(np.mean(nrm2 - 1.0))
+    assert float(np.abs(nrm2 - 1.0).max()) < 5e-6
