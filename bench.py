@@ -249,6 +249,96 @@ def cpu_baseline(name, q, seconds):
                       "one-row-at-a-time operator application, %.1f s" % (rows, q, name, el)}
 
 
+def _spmm_rows(args):
+    """Worker: its row block of the oracle's CSR H times V, reps times;
+    returns its own elapsed seconds."""
+    Hb, V, reps = args
+    Hb @ V
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        Hb @ V
+    return time.perf_counter() - t0
+
+
+def _oracle_ttn_child(name, cap_q):
+    """Child process (one BLAS thread): the oracle's Lanczos (Alg. 1, full
+    reorthogonalisation twice) to the workload's nev at 1e-10 ||H||."""
+    from oracle import basis as ob
+    from oracle import hamiltonian as oh
+    from oracle import lanczos as ol
+    w, sa, sb, inter = synth.workload(name)
+    B = ob.ProductBasis(sa.twom, w.nA, sb.twom, w.nB, w.twoM)
+    H = oh.assemble(B, inter)
+    ev = np.linalg.eigvalsh(H.toarray()) if B.dim <= 4000 else None
+    normH = max(abs(ev[0]), abs(ev[-1])) if ev is not None else json.load(
+        open(os.path.join(ROOT, "tests", "golden", "eigs_%s.json" % name)))["normH"]
+    v1 = synth.random_block(B.dim, 1, 5)[:, 0]
+    t0 = time.perf_counter()
+    theta, X, res, it = ol.lanczos(lambda x: H @ x, B.dim, w.nev, 1e-10, normH, v1, max_iter=min(B.dim, 3000))
+    cap_q.put({"seconds": time.perf_counter() - t0, "iterations": it, "nev": w.nev, "dim": B.dim})
+
+
+def cpu_oracle_extra(cap_seconds=120.0):
+    """The oracle's CSR product H V on the 28,503-dim workload (q = 8) on one
+    core and with row blocks over all host cores, and the oracle's time to
+    nev eigenpairs (Lanczos, one BLAS thread) on the 640- and 28,503-dim
+    workloads, each capped at cap_seconds."""
+    import multiprocessing as mp
+    from oracle import basis as ob
+    from oracle import hamiltonian as oh
+    name = "s12_4p4n"
+    w, sa, sb, inter = synth.workload(name)
+    t0 = time.perf_counter()
+    B = ob.ProductBasis(sa.twom, w.nA, sb.twom, w.nB, w.twoM)
+    H = oh.assemble(B, inter).tocsr()
+    t_asm = time.perf_counter() - t0
+    V = synth.random_block(B.dim, w.q, 1)
+    reps = 20
+    t1 = _spmm_rows((H, V, reps)) / reps
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    # row blocks of about equal nonzeros
+    cuts = np.searchsorted(H.indptr, np.linspace(0, H.nnz, cores + 1)).tolist()
+    cuts[0], cuts[-1] = 0, B.dim
+    blocks = [H[cuts[i]:cuts[i + 1]] for i in range(cores) if cuts[i + 1] > cuts[i]]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(blocks)) as pool:
+        tall = max(pool.map(_spmm_rows, [(b, V, reps) for b in blocks])) / reps
+    out = {"csr_spmm": {"workload": name, "dim": B.dim, "nnz": int(H.nnz), "q": w.q,
+                        "assembly_s": t_asm,
+                        "one_core": {"gnzq_per_s": H.nnz * w.q / t1 / 1e9, "ms": t1 * 1e3},
+                        "all_cores": {"cores": len(blocks), "gnzq_per_s": H.nnz * w.q / tall / 1e9,
+                                      "ms": tall * 1e3, "sample": "row blocks of equal nonzeros, one per "
+                                                                  "spawned process, slowest block's time"}}}
+    ttn = {}
+    saved = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        for nm in ("s12_2p2n", "s12_4p4n"):
+            q = ctx.Queue()
+            pr = ctx.Process(target=_oracle_ttn_child, args=(nm, q))
+            t0 = time.perf_counter()
+            pr.start()
+            pr.join(cap_seconds)
+            if pr.is_alive():
+                pr.terminate()
+                pr.join()
+                ttn[nm] = {"finished": False, "cap_s": cap_seconds}
+            else:
+                r = q.get() if not q.empty() else {}
+                r.update({"finished": bool(r), "wall_s_with_assembly": time.perf_counter() - t0})
+                ttn[nm] = r
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    out["time_to_nev"] = {"method": "oracle Lanczos (Alg. 1, full reorthogonalisation twice), FP64, tol 1e-10 "
+                                    "||H||, one BLAS thread", "cores": 1, **ttn}
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -325,17 +415,32 @@ def run_ours(args, rank, world):
     b_slab = 4 * q * (R + D)  # bytes per apply, FP32
 
     stream = torch.cuda.current_stream()
-    # launch shape of the product: the autotuner times 16, 32, 64 and 128
-    # neutron rows per work item and keeps the fastest (results do not change)
+    # launch shape of the product: the autotuner times every (kernel, rows per
+    # work item, blocks per SM) shape and keeps the fastest (results do not change)
     tune_ms, tune_rows = trbl.apply_autotune(th, q, trbl.TRBL_F32)
+    shape = trbl.apply_get_shape(th)
     torch.cuda.empty_cache()
-    sv = trbl.Solver(th, w.nev, q, w.max_basis, w.tol, precision=trbl.TRBL_PREC_MIXED, seed=w.seed,
-                     check_every=1, stream=stream)
+
+    def steady_solver():
+        # a solver in its steady state: taken through its first thick restart
+        # (basis filled to max_basis, Ritz vectors kept, refilled) before the
+        # warm-up steps, so that the timed steps see the basis fills and the
+        # restarts of a long solve; Rayleigh-Ritz at the solver's own adaptive
+        # cadence, as in a solve
+        s_ = trbl.Solver(th, w.nev, q, w.max_basis, w.tol, precision=trbl.TRBL_PREC_MIXED, seed=w.seed,
+                         check_every=0, stream=stream)
+        while s_.stats()["restarts"] < 1:
+            s_.step()
+        return s_
+
+    sv = steady_solver()
+    fill0 = sv.fill()
     for _ in range(args.warmup):
         sv.step()
     torch.cuda.synchronize()
     barrier()
     st0 = sv.stats()
+    fill1 = sv.fill()
     l0 = trbl.trbl_kernel_launches()
     clocks = ClockSampler(dev)
     clocks.start()
@@ -352,6 +457,7 @@ def run_ours(args, rank, world):
     clk = clocks.stop()
     launches = trbl.trbl_kernel_launches() - l0
     st1 = sv.stats()
+    fill2 = sv.fill()
     ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     ms_step = ms / args.steps
     value = job_throughput(nnz * q * args.steps, ms * 1e-3, world) / 1e9
@@ -360,16 +466,16 @@ def run_ours(args, rank, world):
     traffic, _ = ncu_traffic(tune_rows)
 
     # end to end: the same block steps as the device-timed region (a fresh
-    # solver through the same warm-up, whose last step fills the host copy
-    # of the block), with V_k supplied from and V_{k+1} returned to pinned
-    # host memory through the C ABI (trbl_solver_step_host)
+    # solver through the same set-up and warm-up, whose last step fills the
+    # host copy of the block), with V_k supplied from and V_{k+1} returned to
+    # page-locked host memory on the GPU's nearest memory node
+    # (trbl_host_alloc) through the C ABI (trbl_solver_step_host)
     del sv
     torch.cuda.synchronize()
-    sv = trbl.Solver(th, w.nev, q, w.max_basis, w.tol, precision=trbl.TRBL_PREC_MIXED, seed=w.seed,
-                     check_every=1, stream=stream)
+    sv = steady_solver()
     ptr, nbytes = sv.block()
-    host_in = torch.empty(nbytes // 4, dtype=torch.float32, pin_memory=True)
-    host_out = torch.empty_like(host_in, pin_memory=True)
+    host_in = trbl.HostBuffer(nbytes, dev)
+    host_out = trbl.HostBuffer(nbytes, dev)
     for _ in range(args.warmup - 1):
         sv.step()
     sv.step_host(None, host_in)
@@ -385,6 +491,10 @@ def run_ours(args, rank, world):
     se1 = sv.stats()
     e2e_value = job_throughput(nnz * q * args.steps, el, world) / 1e9
     e2e_phase_ms = sum(se1[k] - se0[k] for k in ("ms_apply", "ms_orth", "ms_qr", "ms_ritz", "ms_restart"))
+    copy_ms = el * 1e3 - e2e_phase_ms
+    numa = host_in.numa_node
+    host_in.free()
+    host_out.free()
 
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
@@ -394,18 +504,26 @@ def run_ours(args, rank, world):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "dim": D, "q": q, "nev": w.nev, "max_basis": w.max_basis,
                    "precision": "mixed (FP32 vectors/apply, FP64 coefficients, CholQR2, Ritz)",
-                   "structural_nnz": nnz, "basis_fill_at_first_timed_step": q * (args.warmup + 1),
+                   "structural_nnz": nnz,
+                   "steps": "steady state: the solver is taken through its first thick restart before the "
+                            "warm-up; Rayleigh-Ritz at the solver's adaptive cadence",
+                   "basis_fill": {"after_first_restart": fill0, "first_timed_step": fill1, "after_timed_steps": fill2},
+                   "restarts_in_timed_region": st1["restarts"] - st0["restarts"],
                    "l2": "inputs larger than L2 (basis %.1f GB, block %.2f GB)"
                          % (D * w.max_basis * 4 / 1e9, D * q * 4 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "apply": {"ms_per_launch": ms_apply, "gnzq_per_s": nnz * q / (ms_apply * 1e-3) / 1e9,
                   "share_of_step": ms_apply / ms_step,
-                  "autotune": {"rows_per_item": [16, 32, 64, 128], "ms": tune_ms, "chosen": tune_rows}},
+                  "autotune": {"shapes": "(kernel, rows per item, blocks per SM): grouped 16/32/64/128 at 8; "
+                                         "fast 16/32/64 at 8; fast 16/32/64 at 6",
+                               "ms": tune_ms, "chosen": {"kernel": ["grouped", "fast"][shape[0]],
+                                                         "rows_per_item": shape[1], "blocks_per_sm": shape[2]}}},
         "phases_ms_per_step": {k: (st1[k] - st0[k]) / args.steps
                                for k in ("ms_apply", "ms_orth", "ms_qr", "ms_ritz", "ms_restart")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "apply_grouped_kernel<float, 8, 1>",
+                     "kernel": ("apply_fast_kernel<8, %d, false>" % shape[2]) if shape[0] == 1
+                               else "apply_grouped_kernel<float, 8, 1>",
                      "algorithmic_bytes_per_launch": b_slab,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"},
         "clocks": clk,
@@ -413,7 +531,10 @@ def run_ours(args, rank, world):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes, "ms_per_step": el / args.steps * 1e3,
                 "steps": "the device-timed block steps, on a fresh solver",
-                "solver_phase_ms_per_step": e2e_phase_ms / args.steps},
+                "solver_phase_ms_per_step": e2e_phase_ms / args.steps,
+                "host_buffers": "trbl_host_alloc, NUMA node %d" % numa if numa >= 0
+                                else "trbl_host_alloc (cudaMallocHost: no NUMA node reported)",
+                "copy_gb_per_s": 2 * nbytes * args.steps / (copy_ms * 1e-3) / 1e9 if copy_ms > 0 else None},
     }
     if rank == 0 and world == 1 and not args.no_proj:
         del sv
@@ -421,11 +542,22 @@ def run_ours(args, rank, world):
         torch.cuda.empty_cache()
         line["projections"] = projections_at(trbl, D, 640, q, peak)
     if rank == 0 and world == 1 and not args.no_ttn:
-        line["time_to_nev"] = time_to_nev(trbl)
+        ttn = {"s12_4p4n": time_to_nev(trbl)}
+        if not args.no_ttn_large:
+            # the headline solves: the 48Cr-sized space (nev 200, basis 1024):
+            # mixed block q = 16, FP64 block q = 16, FP64 Lanczos q = 1; the
+            # 18.6M-dim space (nev 500, basis 1024): mixed q = 32
+            ttn["s20_4p4n"] = time_to_nev_large(
+                trbl, "s20_4p4n", (("fp64_q16", trbl.TRBL_PREC_F64, 16), ("mixed_q16", trbl.TRBL_PREC_MIXED, 16),
+                                   ("fp64_q1", trbl.TRBL_PREC_F64, 1)))
+            ttn[args.workload] = time_to_nev_large(trbl, args.workload,
+                                                   (("mixed_q%d" % q, trbl.TRBL_PREC_MIXED, q),), th=th)
+        line["time_to_nev"] = ttn
     if rank == 0 and world == 1 and not args.no_batch:
         line["gradient_batch"] = gradient_batch(trbl)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, q, args.cpu_seconds)
+        line["cpu_baseline"]["oracle_extra"] = cpu_oracle_extra()
     del sv
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -500,27 +632,28 @@ def time_to_nev(trbl, name="s12_4p4n"):
     return out
 
 
-def time_to_nev_large(trbl, name, arms):
+def time_to_nev_large(trbl, name, arms, th=None):
     """Full solves of a large workload to residual 1e-6 ||H|| (no stored
     oracle eigenvalues at this size): each arm's eigenvalues are compared
     with the first arm's, and every arm reports its true residuals (FP64
-    apply).  Each timed solve follows an untimed one that stops after its
-    first restart, so that one-time library loading is not counted.  arms:
-    (label, precision, q) tuples."""
+    apply).  Each timed solve follows a short untimed one (3 block steps),
+    so that first-use kernel loading is not counted.  arms: (label,
+    precision, q) tuples; th: the workload's Hamiltonian if already built."""
     import torch
     w, sa, sb, inter = synth.workload(name)
-    tb = trbl.Basis(sa, w.nA, sb, w.nB, w.twoM)
-    th = trbl.Hamiltonian.from_interaction(tb, inter)
+    if th is None:
+        tb = trbl.Basis(sa, w.nA, sb, w.nB, w.twoM)
+        th = trbl.Hamiltonian.from_interaction(tb, inter)
     tune_ms, tune_rows = trbl.apply_autotune(th, w.q, trbl.TRBL_F32)
+    shape = trbl.apply_get_shape(th)
     torch.cuda.empty_cache()
-    out = {"workload": name, "dim": tb.dim, "nev": w.nev, "max_basis": w.max_basis, "tol_rel_normH": 1e-6,
-           "rows_per_item": tune_rows}
+    out = {"workload": name, "dim": th.basis.dim, "nev": w.nev, "max_basis": w.max_basis, "tol_rel_normH": 1e-6,
+           "product_shape": {"kernel": ["grouped", "fast"][shape[0]], "rows_per_item": shape[1],
+                             "blocks_per_sm": shape[2]}}
     first = None
     for label, prec, q in arms:
-        # untimed warm-up through the first restart: the libraries' kernels for these
-        # sizes (eigensolver, restart GEMM) load on first use in a process
         trbl.solve(th, w.nev, q, w.max_basis, 1e-6, precision=prec, want_vectors=False, raise_on_noconv=False,
-                   max_iter=w.max_basis // q + 2)
+                   max_iter=3)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ev, rs, X, st = trbl.solve(th, w.nev, q, w.max_basis, 1e-6, precision=prec, want_vectors=False,
@@ -669,6 +802,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttn", action="store_true", help="skip the time-to-nev solves")
+    ap.add_argument("--no-ttn-large", action="store_true",
+                    help="skip the time-to-nev solves of the 2M- and 18.6M-dim workloads")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-set gradient batch")
     ap.add_argument("--no-proj", action="store_true", help="skip the projection kernels' own timing")
     ap.add_argument("--arms", default=None, metavar="LABEL,...",

@@ -281,6 +281,8 @@ typedef struct trbl_stats {
   int status;          /* return value of trbl_solve */
   double normH;        /* ||H|| used by the tolerance */
   double ms_total, ms_apply, ms_orth, ms_qr, ms_ritz, ms_restart;
+  int basis_size;      /* Lanczos vectors in the basis now (stepwise solver; the last step's for trbl_solve) */
+  int pad_;
 } trbl_stats;
 
 /* Lowest nev eigenpairs of H by the thick-restart block Lanczos method
@@ -387,7 +389,49 @@ int trbl_apply_set_compensated(trbl_hamiltonian* h, int on);
  *   vectors of the current basis, as trbl_solve returns them; TRBL_ERR_NOCONV
  *   when not all nev pairs met the tolerance (outputs still filled).
  * trbl_solver_destroy: synchronises the stream and frees the solver. */
+/* Row sharding of the block product over several GPUs (the paper's
+ * distributed matrix-vector product, App. C, with every GPU holding the
+ * tables): rows of W are split into contiguous ranges of whole target slabs
+ * (the rows (pA', nB') of one proton determinant pA'); a shard's product
+ * reads the slabs of its targets' source proton determinants, which the
+ * shard receives from the others before the product (an all-gather of V
+ * slices, or only the listed ranges), and the projections are sharded by the
+ * same rows with the m x q coefficients summed across shards.  All host
+ * only; they need no GPU.
+ *
+ * trbl_shard_plan: bounds[nranks + 1] (host) receives slab-aligned row
+ *   boundaries, bounds[0] = 0 and bounds[nranks] = D, balanced by the
+ *   elements the product generates per row (the cross term's proton x
+ *   neutron jump pairs, plus one for a row's like-particle and diagonal
+ *   work); work[nranks] (host, may be NULL) the estimate per shard.
+ * trbl_shard_sources: the V rows the product of rows [row_begin, row_end)
+ *   reads, as *nranges merged [begin, end) pairs in ranges[2 * cap] (host;
+ *   NULL with cap 0 only counts).  The rows must be slab boundaries. */
+int trbl_shard_plan(const trbl_basis* b, int nranks, int64_t* bounds, int64_t* work);
+int trbl_shard_sources(const trbl_basis* b, int64_t row_begin, int64_t row_end, int64_t* ranges, int64_t cap,
+                       int64_t* nranges);
+
+/* Restricts the product of h (trbl_apply_block) to rows [row_begin,
+ * row_end) of W, slab boundaries of the basis (0 and D restore the whole
+ * product); the other rows of W are not written.  Needs the grouped or fast
+ * kernel (16-byte aligned rows of q * element size = 16 * 2^i bytes), and
+ * the solvers need the whole product.  Host only; not while a product of h
+ * is running.  Errors: TRBL_ERR_ARG. */
+int trbl_hamiltonian_set_rows(trbl_hamiltonian* h, int64_t row_begin, int64_t row_end);
+
 typedef struct trbl_solver trbl_solver;
+
+/* Page-locked host memory on the host memory node closest to `device`
+ * (cudaDevAttrHostNumaId), for the blocks of trbl_solver_step_host: the
+ * copies then cross only the GPU's own link to that node.  The pages are
+ * bound to the node (mbind) and touched before they are registered with
+ * CUDA; where the device names no node or the binding is refused the buffer
+ * is cudaMallocHost memory and *numa_node is -1 (numa_node may be NULL).
+ * The caller owns the buffer and frees it with trbl_host_free.  Errors:
+ * TRBL_ERR_ARG, TRBL_ERR_OOM, TRBL_ERR_CUDA. */
+int trbl_host_alloc(size_t bytes, int device, void** out, int* numa_node);
+int trbl_host_free(void* p);
+
 int trbl_solver_create(const trbl_hamiltonian* h, const trbl_params* p, void* stream, trbl_solver** out);
 int trbl_solver_step(trbl_solver* s, int* converged);
 int trbl_solver_step_host(trbl_solver* s, const void* block_in, void* block_out, int* converged);

@@ -23,5 +23,5 @@ from ._lib import (  # noqa: F401
     trbl_solver_stats, trbl_solver_destroy, trbl_solver_state_bytes, trbl_solver_save, trbl_solver_load,
     trbl_param_count, trbl_grad, arrays_from_theta, clusters_of, hf_gradient, hf_gradient_clusters, LowestEigenvalues,
     solve_batch, apply_autotune, apply_set_rows, apply_set_shape, apply_get_shape, apply_set_compensated,
-    Basis, Hamiltonian, Solver, solve,
+    Basis, Hamiltonian, Solver, HostBuffer, shard_plan, shard_sources, solve,
 )

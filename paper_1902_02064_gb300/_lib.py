@@ -45,7 +45,7 @@ class trbl_stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
                 ("status", C.c_int), ("normH", C.c_double), ("ms_total", C.c_double),
                 ("ms_apply", C.c_double), ("ms_orth", C.c_double), ("ms_qr", C.c_double),
-                ("ms_ritz", C.c_double), ("ms_restart", C.c_double)]
+                ("ms_ritz", C.c_double), ("ms_restart", C.c_double), ("basis_size", C.c_int), ("pad_", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -105,6 +105,12 @@ def lib():
         "trbl_apply_set_shape": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int]),
         "trbl_apply_get_shape": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "trbl_apply_set_compensated": (C.c_int, [_VP, C.c_int]),
+        "trbl_host_alloc": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(_VP), C.POINTER(C.c_int)]),
+        "trbl_host_free": (C.c_int, [_VP]),
+        "trbl_shard_plan": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        "trbl_shard_sources": (C.c_int, [_VP, C.c_int64, C.c_int64, C.POINTER(C.c_int64), C.c_int64,
+                                         C.POINTER(C.c_int64)]),
+        "trbl_hamiltonian_set_rows": (C.c_int, [_VP, C.c_int64, C.c_int64]),
         "trbl_kernel_launches": (C.c_longlong, []),
         "trbl_last_error": (C.c_char_p, []),
     }
@@ -326,6 +332,11 @@ class Hamiltonian:
                          V.shape[1], dt, s.cuda_stream)
         return W
 
+    def set_rows(self, row_begin: int, row_end: int):
+        """Restrict the product to W rows [row_begin, row_end) (slab boundaries;
+        0 and D restore the whole product)."""
+        _check(lib().trbl_hamiltonian_set_rows(self.handle, int(row_begin), int(row_end)))
+
     def __del__(self):
         if getattr(self, "handle", None) and _LIB is not None:
             _LIB.trbl_hamiltonian_destroy(self.handle)
@@ -413,6 +424,54 @@ def trbl_solver_load(sv: int, host_ptr: int, nbytes: int):
     _check(lib().trbl_solver_load(sv, host_ptr, nbytes))
 
 
+def shard_plan(basis: "Basis", nranks: int):
+    """(bounds[nranks + 1], work[nranks]): slab-aligned row ranges of W
+    balanced by generated elements (trbl_shard_plan)."""
+    bounds = (C.c_int64 * (nranks + 1))()
+    work = (C.c_int64 * nranks)()
+    _check(lib().trbl_shard_plan(basis.handle, int(nranks), bounds, work))
+    return list(bounds), list(work)
+
+
+def shard_sources(basis: "Basis", row_begin: int, row_end: int):
+    """[(begin, end), ...]: the V rows the product of W rows [row_begin,
+    row_end) reads (trbl_shard_sources)."""
+    n = C.c_int64()
+    _check(lib().trbl_shard_sources(basis.handle, int(row_begin), int(row_end), None, 0, C.byref(n)))
+    r = (C.c_int64 * (2 * max(n.value, 1)))()
+    _check(lib().trbl_shard_sources(basis.handle, int(row_begin), int(row_end), r, n.value, C.byref(n)))
+    return [(r[2 * i], r[2 * i + 1]) for i in range(n.value)]
+
+
+class HostBuffer:
+    """Page-locked host memory on the GPU's nearest host memory node
+    (trbl_host_alloc); .array is a numpy view, .ptr the address, .numa_node
+    the node (-1 for plain pinned memory)."""
+
+    def __init__(self, nbytes: int, device: int = 0, dtype=np.float32):
+        p, node = _VP(), C.c_int()
+        _check(lib().trbl_host_alloc(int(nbytes), int(device), C.byref(p), C.byref(node)))
+        self.ptr, self.nbytes, self.numa_node = p.value, int(nbytes), node.value
+        n = int(nbytes) // np.dtype(dtype).itemsize
+        buf = (C.c_char * int(nbytes)).from_address(self.ptr)
+        self.array = np.frombuffer(buf, dtype=dtype, count=n)
+
+    def data_ptr(self) -> int:
+        return self.ptr
+
+    def free(self):
+        if getattr(self, "ptr", None):
+            self.array = None
+            _check(lib().trbl_host_free(self.ptr))
+            self.ptr = None
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _LIB is not None:
+            self.array = None
+            _LIB.trbl_host_free(self.ptr)
+            self.ptr = None
+
+
 class Solver:
     """Stepwise thick-restart block Lanczos (trbl_solver_* entry points)."""
 
@@ -453,6 +512,10 @@ class Solver:
 
     def stats(self) -> dict:
         return trbl_solver_stats(self.handle)
+
+    def fill(self) -> int:
+        """Lanczos vectors in the basis now."""
+        return self.stats()["basis_size"]
 
     def finish(self, want_vectors: bool = True, raise_on_noconv: bool = True):
         import torch

@@ -219,6 +219,9 @@ int launch_apply(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W,
                  int q, int dtype, cudaStream_t s) {
   const int g = launch_grouped(h, V, ldv, W, ldw, q, dtype, s);
   if (g != -1) return g;
+  if (h->row_end >= 0 && (h->row_begin != 0 || h->row_end != h->b->D))
+    return fail(TRBL_ERR_ARG, "a row-restricted product needs 16-byte aligned rows of q * element size = 16 * 2^i "
+                              "bytes (the grouped and fast kernels)");
   const int64_t D = h->b->D;
   if (dtype == TRBL_F64)
     return launch_typed<double>(h->d64, D, static_cast<const double*>(V), ldv,

@@ -449,14 +449,20 @@ int set_work_items(trbl_hamiltonian* h, int rows_per_item) {
   const trbl_basis* b = h->b;
   const Species& A = b->sp[0];
   std::vector<int4> work;
+  const int64_t rb = h->row_begin, re = h->row_end < 0 ? b->D : h->row_end;
   for (size_t k = 0; k < b->blocks.size(); ++k) {
     const Block& bl = b->blocks[k];
     const int a0 = A.gfirst[bl.gA];
-    for (int ia = 0; ia < bl.na; ++ia)
+    for (int ia = 0; ia < bl.na; ++ia) {
+      const int64_t slab = bl.off + int64_t(ia) * bl.nb;
+      if (slab < rb || slab >= re) continue;
       for (int r0 = 0; r0 < bl.nb; r0 += rows_per_item)
         work.push_back(make_int4(a0 + ia, int(k), r0, std::min(rows_per_item, bl.nb - r0)));
+    }
   }
   if (work.size() > size_t(0x7fffffff)) return fail(TRBL_ERR_ARG, "too many work items");
+  if (work.empty())  // a shard without rows: one item of zero rows
+    work.push_back(make_int4(A.gfirst[b->blocks[0].gA], 0, 0, 0));
   void* p = nullptr;
   TRBL_CUDA(cudaMalloc(&p, work.size() * sizeof(int4)));
   cudaError_t e = cudaMemcpy(p, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice);

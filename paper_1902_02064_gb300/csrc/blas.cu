@@ -381,6 +381,90 @@ __global__ void __launch_bounds__(512) rowgemm_tall_kernel(const T* __restrict__
   }
 }
 
+// Narrow forms for q (resp. n) <= NQ <= 4 columns: the one-vector Lanczos
+// (q = 1) and the column-wise QR.  The wide kernels above compute 4 x 4
+// register tiles, so up to 15 of 16 products would be padding; in FP64,
+// whose FMA rate is a small fraction of FP32's, that padding dominated.
+//
+// partial[chunk][i][j] = sum over the chunk's rows r of B[r, i] W[r, j]:
+// thread = one column i of B (256 consecutive columns per block, coalesced
+// row reads), W's row broadcast to all threads.  FP32 data sum 32-row
+// segments before adding them to the running sum.
+template <typename T, int NQ>
+__global__ void __launch_bounds__(256) dot_narrow_kernel(const T* __restrict__ B, int64_t ldb, int m,
+                                                        const T* __restrict__ W, int64_t ldw, int q, int64_t D,
+                                                        int64_t rows_per_chunk, double* __restrict__ partial) {
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  const int64_t r0 = int64_t(blockIdx.y) * rows_per_chunk;
+  const int64_t r1 = min(D, r0 + rows_per_chunk);
+  T acc[NQ];
+#pragma unroll
+  for (int j = 0; j < NQ; ++j) acc[j] = T(0);
+  if (i < m) {
+    for (int64_t r = r0; r < r1; r += 32) {
+      const int64_t re = min(r1, r + 32);
+      T t[NQ];
+#pragma unroll
+      for (int j = 0; j < NQ; ++j) t[j] = T(0);
+      for (int64_t rr = r; rr < re; ++rr) {
+        const T b = B[rr * ldb + i];
+#pragma unroll
+        for (int j = 0; j < NQ; ++j)
+          if (j < q) t[j] = fma(b, __ldg(W + rr * ldw + j), t[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < NQ; ++j) acc[j] += t[j];
+    }
+    double* P = partial + int64_t(blockIdx.y) * m * q + int64_t(i) * q;
+#pragma unroll
+    for (int j = 0; j < NQ; ++j)
+      if (j < q) P[j] = double(acc[j]);
+  }
+}
+
+// Out[r, 0:n] = alpha In[r, 0:K] U + beta Out[r, 0:n], n <= NQ: a warp per
+// row (lanes stride over K, coalesced), U staged in shared memory, the
+// lanes' partial sums combined by shuffles; persistent blocks of 8 warps.
+template <typename T, int NQ>
+__global__ void __launch_bounds__(256) rowgemm_narrow_kernel(const T* __restrict__ In, int64_t ldi, int K,
+                                                            const double* __restrict__ U, int64_t ldu, int n,
+                                                            T* __restrict__ Out, int64_t ldo, int64_t D, double alpha,
+                                                            double beta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Us = reinterpret_cast<T*>(smem_raw);  // [K][NQ]
+  for (int e = threadIdx.x; e < K * NQ; e += 256) {
+    const int k = e / NQ, c = e - k * NQ;
+    Us[e] = c < n ? T(U[int64_t(k) * ldu + c]) : T(0);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = int64_t(gridDim.x) * 8;
+  for (int64_t r = int64_t(blockIdx.x) * 8 + (threadIdx.x >> 5); r < D; r += warps) {
+    const T* row = In + r * ldi;
+    T acc[NQ];
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) acc[c] = T(0);
+    for (int k = lane; k < K; k += 32) {
+      const T x = row[k];
+#pragma unroll
+      for (int c = 0; c < NQ; ++c) acc[c] = fma(x, Us[k * NQ + c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < NQ; ++c)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    if (lane < n) {
+      T v = acc[0];
+#pragma unroll
+      for (int c = 1; c < NQ; ++c)
+        if (lane == c) v = acc[c];
+      T* o = Out + r * ldo + lane;
+      const T a = T(alpha) * v;
+      *o = (beta == 0.0) ? a : fma(T(beta), *o, a);
+    }
+  }
+}
+
 template <typename T>
 __global__ void scale_col_kernel(T* __restrict__ X, int64_t ldx, int64_t D, double a) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -460,6 +544,55 @@ int dot_launch_capped(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, i
   TRBL_CUDA(cudaGetLastError());
   const int mq = m * q;
   reduce_partials_kernel<<<(mq + 255) / 256, 256, 0, s>>>(partial, int(nchunk), mq, C); note_launch();
+  TRBL_CUDA(cudaGetLastError());
+  return TRBL_OK;
+}
+
+// block_dot for q <= 4 through dot_narrow_kernel; the chunk count fits the
+// workspace that block_dot_workspace_bytes sizes for the same m and q.
+template <typename T>
+int dot_narrow(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, int64_t D, double* C, Workspace& ws,
+               cudaStream_t s) {
+  const int mt = (m + 255) / 256;
+  const int64_t fit = int64_t(ws.partial_bytes / (size_t(m) * q * sizeof(double)));
+  if (fit < 1) return fail(TRBL_ERR_ARG, "block_dot workspace too small");
+  int64_t nchunk = std::max<int64_t>(1, std::min<int64_t>((4 * ws.sm_count + mt - 1) / mt, fit));
+  nchunk = std::min<int64_t>(nchunk, (D + 31) / 32);
+  int64_t rows = (D + nchunk - 1) / nchunk;
+  rows = (rows + 31) / 32 * 32;
+  nchunk = (D + rows - 1) / rows;
+  const dim3 grid{unsigned(mt), unsigned(nchunk), 1u};
+  if (q == 1)
+    dot_narrow_kernel<T, 1><<<grid, 256, 0, s>>>(B, ldb, m, W, ldw, q, D, rows, ws.partial);
+  else if (q == 2)
+    dot_narrow_kernel<T, 2><<<grid, 256, 0, s>>>(B, ldb, m, W, ldw, q, D, rows, ws.partial);
+  else
+    dot_narrow_kernel<T, 4><<<grid, 256, 0, s>>>(B, ldb, m, W, ldw, q, D, rows, ws.partial);
+  note_launch();
+  TRBL_CUDA(cudaGetLastError());
+  const int mq = m * q;
+  reduce_partials_kernel<<<(mq + 255) / 256, 256, 0, s>>>(ws.partial, int(nchunk), mq, C);
+  note_launch();
+  TRBL_CUDA(cudaGetLastError());
+  return TRBL_OK;
+}
+
+template <typename T, int NQ>
+int narrow_launch(const T* In, int64_t ldi, int K, const double* U, int64_t ldu, int n, T* Out, int64_t ldo,
+                  int64_t D, double alpha, double beta, cudaStream_t s) {
+  static const cudaError_t cfg = cudaFuncSetAttribute(rowgemm_narrow_kernel<T, NQ>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  TRBL_CUDA(cfg);
+  static const int sms = [] {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 148;
+  }();
+  const size_t smem = size_t(K) * NQ * sizeof(T);
+  const int64_t blocks = std::min<int64_t>((D + 7) / 8, int64_t(sms) * 4);
+  rowgemm_narrow_kernel<T, NQ><<<unsigned(blocks), 256, smem, s>>>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta);
+  note_launch();
   TRBL_CUDA(cudaGetLastError());
   return TRBL_OK;
 }
@@ -584,6 +717,7 @@ int block_dot(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, in
     const int rc = block_dot_tma(B, ldb, m, W, ldw, q, D, C, ws.partial, ws.partial_bytes, ws.sm_count, s);
     if (rc != -1) return rc;
   }
+  if (std::is_same<T, double>::value && q <= 4) return dot_narrow<T>(B, ldb, m, W, ldw, q, D, C, ws, s);
   if (q <= 4) return dot_launch<T, 4>(B, ldb, m, W, ldw, q, D, C, ws, s);
   if (q <= 8) return dot_launch<T, 8>(B, ldb, m, W, ldw, q, D, C, ws, s);
   if (q <= 16) return dot_launch<T, 16>(B, ldb, m, W, ldw, q, D, C, ws, s);
@@ -619,6 +753,11 @@ int rowgemm(const T* In, int64_t ldi, int K, const double* U, int64_t ldu, int n
       const int rc = rowgemm_tma(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta, s);
       if (rc != -1) return rc;
     }
+  }
+  if (std::is_same<T, double>::value && K > 0 && n <= 4 && size_t(K) * 4 * sizeof(T) <= 200 * 1024) {
+    if (n == 1) return narrow_launch<T, 1>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta, s);
+    if (n == 2) return narrow_launch<T, 2>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta, s);
+    return narrow_launch<T, 4>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta, s);
   }
   if (K > 0 && n <= 64) {
     const int NP = n <= 16 ? 16 : (n <= 32 ? 32 : 64);

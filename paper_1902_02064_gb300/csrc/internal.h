@@ -123,6 +123,7 @@ struct trbl_hamiltonian {
   int apply_kernel = TRBL_APPLY_FAST;  // FP32 product: TRBL_APPLY_FAST where it applies, else the grouped kernel
   int blocks_per_sm = 8;   // resident thread blocks per SM the FP32 fast kernel is compiled for (8 or 6)
   int apply_compensated = 0;  // FP32 fast kernel: compensated (TwoSum) row sums
+  int64_t row_begin = 0, row_end = -1;  // rows of W the product computes (slab-aligned; -1: all)
   void* grad = nullptr;  // gradient tables, built on the first trbl_grad call
   size_t arena_bytes = 0;
 };
@@ -135,8 +136,11 @@ namespace trbl {
 int upload_tables(trbl_hamiltonian* h);
 // Builds and uploads the grouped-kernel tables (apply_grouped.cu).
 int upload_grouped(trbl_hamiltonian* h);
-// Replaces the grouped kernel's work items (rows_per_item rows each).
+// Replaces the grouped kernel's work items (rows_per_item rows each), for
+// the target slabs inside the Hamiltonian's row range.
 int set_work_items(trbl_hamiltonian* h, int rows_per_item);
+// Whether row r starts a target slab of the basis (0 and D count).
+bool is_slab_boundary(const trbl_basis* b, int64_t r);
 // Dynamic shared memory of the grouped kernel for one Hamiltonian.
 size_t grouped_smem_bytes(const trbl_hamiltonian* h, int dtype);
 // One launch of the grouped kernel over nset Hamiltonians (device arrays of

@@ -794,6 +794,7 @@ struct Solver {
     st->ms_qr = ms_qr;
     st->ms_ritz = ms_ritz;
     st->ms_restart = ms_restart;
+    st->basis_size = nb;
   }
 
   // ---- checkpoint: the state between block steps ----
@@ -954,6 +955,8 @@ struct Solver {
     tau = dtype == TRBL_F64 ? 1e-10 : 1e-4;
     tau_max = dtype == TRBL_F64 ? 1e-6 : 1e-3;
     if (q < 1 || q > 64) return fail(TRBL_ERR_ARG, "q=%d outside [1, 64]", q);
+    if (h->row_end >= 0 && (h->row_begin != 0 || h->row_end != D))
+      return fail(TRBL_ERR_ARG, "the solver needs the product over all rows (trbl_hamiltonian_set_rows(h, 0, D))");
     if (nev < 1) return fail(TRBL_ERR_ARG, "nev must be positive");
     if (mb > D) return fail(TRBL_ERR_ARG, "max_basis=%d exceeds the dimension %lld", mb, (long long)D);
     if (mb < nev + 2 * q) return fail(TRBL_ERR_ARG, "max_basis must be at least nev + 2q");

@@ -43,3 +43,23 @@ def test_block_dot_strided_and_errors():
     host = np.zeros((D, q))
     with pytest.raises(trbl.TrblError):
         trbl.trbl_block_dot(B.data_ptr(), 64, m, host.ctypes.data, q, q, D, trbl.TRBL_F64, C.data_ptr(), 0)
+
+
+@pytest.mark.parametrize("D,m,q", [(1, 1, 1), (100003, 1024, 1), (70001, 300, 2), (5000, 17, 3), (33333, 600, 4)])
+def test_narrow_fp64_dot_and_update(D, m, q):
+    """FP64 projections with q (resp. n) <= 4 columns -- the one-vector
+    Lanczos arm and the column-wise QR -- through the narrow kernels, against
+    numpy: C = B^T W and Out = alpha B U + beta Out."""
+    B = torch.from_numpy(synth.random_block(D, m, 61)).cuda()
+    W = torch.from_numpy(synth.random_block(D, q, 62)).cuda()
+    C = trbl.block_dot(B, W).cpu().numpy()
+    Bh, Wh = B.cpu().numpy(), W.cpu().numpy()
+    ref = Bh.T @ Wh
+    assert np.all(np.abs(C - ref) <= 1e-12 * (np.abs(Bh).T @ np.abs(Wh)) + 1e-300)
+    U = synth.random_block(m, q, 63)
+    O0 = synth.random_block(D, q, 64)
+    Out = torch.from_numpy(O0.copy()).cuda()
+    trbl.block_update(B, torch.from_numpy(U).cuda(), Out, -1.0, 0.5)
+    ref = -(Bh @ U) + 0.5 * O0
+    bound = np.abs(Bh) @ np.abs(U) + 0.5 * np.abs(O0)
+    assert np.all(np.abs(Out.cpu().numpy() - ref) <= 1e-12 * bound + 1e-300)
