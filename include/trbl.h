@@ -33,6 +33,7 @@
 #ifndef TRBL_H
 #define TRBL_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus

@@ -336,3 +336,29 @@ def test_compensated_sums_match_oracle_and_cut_rounding(medium):
     trbl.apply_set_shape(th, trbl.TRBL_APPLY_FAST, 16, 8)
     print("max |W - HV| / (|H||V|): plain %.2e compensated %.2e" % (errs[False], errs[True]))
     assert errs[True] < errs[False]
+
+
+@pytest.mark.parametrize("dtype,q", [(torch.float32, 32), (torch.float64, 16)])
+def test_row_restricted_products_tile_the_full_product(medium, dtype, q):
+    """The shards of a 3-way plan (trbl_shard_plan), each computed alone with
+    trbl_hamiltonian_set_rows, reproduce the full product's rows bit for bit
+    and leave every other row of W untouched."""
+    w, B, H, tb, th = medium
+    bounds, work = trbl.shard_plan(tb, 3)
+    V = torch.from_numpy(synth.random_block(B.dim, q, 77)).to(dtype).cuda()
+    full = th.apply(V)
+    for r in range(3):
+        th.set_rows(bounds[r], bounds[r + 1])
+        W = torch.full_like(full, 7.0)
+        th.apply(V, W)
+        torch.cuda.synchronize()
+        assert torch.equal(W[bounds[r]:bounds[r + 1]], full[bounds[r]:bounds[r + 1]])
+        assert torch.all(W[:bounds[r]] == 7.0) and torch.all(W[bounds[r + 1]:] == 7.0)
+    th.set_rows(0, tb.dim)
+    assert torch.equal(th.apply(V), full)
+    with pytest.raises(trbl.TrblError):
+        th.set_rows(1, tb.dim)
+    th.set_rows(bounds[1], bounds[2])
+    with pytest.raises(trbl.TrblError):
+        trbl.solve(th, 4, 4, 40, 1e-8)
+    th.set_rows(0, tb.dim)
