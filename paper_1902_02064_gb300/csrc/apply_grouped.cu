@@ -279,11 +279,15 @@ int launch_typed(const trbl_hamiltonian* hm, const DevH<T>& h, const DevG<T>& g,
   if ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(W)) & 15) return -1;
   if ((ldv * int64_t(sizeof(T))) % 16 || (ldw * int64_t(sizeof(T))) % 16) return -1;
   if (int64_t(hm->b->max_group) * ldv >= (int64_t(1) << 31)) return -1;
+  // TRBL_APPLY_GROUPED_X2: half the lanes per element, two 16-byte chunks
+  // each (twice the elements in flight per warp instruction, half the
+  // loads per lane group)
+  const bool x2 = hm->apply_kernel == TRBL_APPLY_GROUPED_X2;
   switch (bytes / 16) {
     case 1: return launch_lpe<T, 1, 1>(h, g, V, ldv, W, ldw, s);
-    case 2: return launch_lpe<T, 2, 1>(h, g, V, ldv, W, ldw, s);
-    case 4: return launch_lpe<T, 4, 1>(h, g, V, ldv, W, ldw, s);
-    case 8: return launch_lpe<T, 8, 1>(h, g, V, ldv, W, ldw, s);  // 8 x 1: 9 % faster than 4 x 2 on 128-byte rows
+    case 2: return x2 ? launch_lpe<T, 1, 2>(h, g, V, ldv, W, ldw, s) : launch_lpe<T, 2, 1>(h, g, V, ldv, W, ldw, s);
+    case 4: return x2 ? launch_lpe<T, 2, 2>(h, g, V, ldv, W, ldw, s) : launch_lpe<T, 4, 1>(h, g, V, ldv, W, ldw, s);
+    case 8: return x2 ? launch_lpe<T, 4, 2>(h, g, V, ldv, W, ldw, s) : launch_lpe<T, 8, 1>(h, g, V, ldv, W, ldw, s);
     case 16: return launch_lpe<T, 4, 4>(h, g, V, ldv, W, ldw, s);
     case 32: return launch_lpe<T, 4, 8>(h, g, V, ldv, W, ldw, s);
     default: return -1;

@@ -1,12 +1,13 @@
 // Autotuner of the block product's launch shape.  Three knobs:
-// * the kernel: the grouped kernel (any q, FP32 or FP64) or the FP32 fast
-//   kernel (rows of 32, 64 or 128 bytes);
+// * the kernel: the grouped kernel (any q, FP32 or FP64), the same with
+//   two 16-byte chunks per lane (half the lanes per element), or the FP32
+//   fast kernel (rows of 32, 64 or 128 bytes);
 // * neutron rows per work item: the grid size, the share of staging work per
 //   thread block and how many target determinants are in flight (L2 reuse);
 // * resident thread blocks per SM the fast kernel is compiled for (8 blocks
 //   at 32 registers a thread, or 6 at 40): warps in flight against
 //   registers per warp.
-// The lanes per element and 16-byte chunks per lane follow from q and the
+// Lanes per element and chunks per lane follow from the kernel, q and the
 // element size (one lane group reads one whole row of V).  Each candidate is
 // timed with CUDA events on the caller's stream and the fastest is kept;
 // the product's results do not depend on the choice.
@@ -28,7 +29,8 @@ constexpr Shape kCand[TRBL_TUNE_CANDIDATES] = {
     {TRBL_APPLY_GROUPED, 16, 8}, {TRBL_APPLY_GROUPED, 32, 8}, {TRBL_APPLY_GROUPED, 64, 8},
     {TRBL_APPLY_GROUPED, 128, 8}, {TRBL_APPLY_FAST, 16, 8},   {TRBL_APPLY_FAST, 32, 8},
     {TRBL_APPLY_FAST, 64, 8},     {TRBL_APPLY_FAST, 16, 6},   {TRBL_APPLY_FAST, 32, 6},
-    {TRBL_APPLY_FAST, 64, 6}};
+    {TRBL_APPLY_FAST, 64, 6},     {TRBL_APPLY_GROUPED_X2, 16, 8}, {TRBL_APPLY_GROUPED_X2, 32, 8},
+    {TRBL_APPLY_GROUPED_X2, 64, 8}};
 
 int set_shape(trbl_hamiltonian* h, const Shape& c) {
   h->apply_kernel = c.kernel;
@@ -55,12 +57,15 @@ extern "C" int trbl_apply_autotune(trbl_hamiltonian* h, int q, int dtype, float*
   cudaEventCreate(&e1);
   const bool fast = dtype == TRBL_F32 && (q == 8 || q == 16 || q == 32) && h->g32.likeB && h->b->ND <= 31 &&
                     h->b->D * q < (int64_t(1) << 31);
+  const int row_bytes = q * (dtype == TRBL_F64 ? 8 : 4);
+  const bool x2 = row_bytes == 32 || row_bytes == 64 || row_bytes == 128;
   float best = 1e30f;
   Shape keep{h->apply_kernel, h->rows_per_item, h->blocks_per_sm};
   int rc = TRBL_OK;
   for (int c = 0; c < TRBL_TUNE_CANDIDATES && !rc; ++c) {
     if (ms) ms[c] = NAN;
     if (kCand[c].kernel == TRBL_APPLY_FAST && !fast) continue;
+    if (kCand[c].kernel == TRBL_APPLY_GROUPED_X2 && !x2) continue;
     rc = set_shape(h, kCand[c]);
     if (rc) break;
     rc = launch_apply(h, V, q, W, q, q, dtype, s);  // warm-up
@@ -97,7 +102,8 @@ extern "C" int trbl_apply_set_rows(trbl_hamiltonian* h, int rows_per_item) {
 extern "C" int trbl_apply_set_shape(trbl_hamiltonian* h, int kernel, int rows_per_item, int blocks_per_sm) {
   clear_error();
   if (!h) return fail(TRBL_ERR_ARG, "null Hamiltonian");
-  if (kernel != TRBL_APPLY_GROUPED && kernel != TRBL_APPLY_FAST) return fail(TRBL_ERR_ARG, "unknown kernel %d", kernel);
+  if (kernel != TRBL_APPLY_GROUPED && kernel != TRBL_APPLY_FAST && kernel != TRBL_APPLY_GROUPED_X2)
+    return fail(TRBL_ERR_ARG, "unknown kernel %d", kernel);
   if (rows_per_item < 1 || rows_per_item > 4096) return fail(TRBL_ERR_ARG, "rows per work item must be in [1, 4096]");
   if (blocks_per_sm != 6 && blocks_per_sm != 8) return fail(TRBL_ERR_ARG, "blocks per SM must be 6 or 8");
   if (!h->garena) return fail(TRBL_ERR_ARG, "the grouped product is not available for this basis");

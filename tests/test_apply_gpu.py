@@ -224,6 +224,7 @@ def test_launch_shape_does_not_change_results(medium):
 
 SHAPES = [(trbl.TRBL_APPLY_GROUPED, 16, 8), (trbl.TRBL_APPLY_FAST, 16, 8), (trbl.TRBL_APPLY_FAST, 64, 6),
           (trbl.TRBL_APPLY_FAST, 1, 8), (trbl.TRBL_APPLY_FAST, 4096, 6)]
+X2 = (trbl.TRBL_APPLY_GROUPED_X2, 32, 8)
 
 
 @pytest.mark.parametrize("q", [8, 16, 32])
@@ -247,6 +248,11 @@ def test_fast_kernel_every_element_matches_oracle(small, medium, q):
         trbl.apply_set_shape(th, trbl.TRBL_APPLY_FAST, 16, 8)
         for o in outs[1:]:
             assert torch.equal(o, outs[0])
+        # two chunks per lane: same products, summed in another lane layout
+        trbl.apply_set_shape(th, *X2)
+        W = th.apply(Vc)
+        torch.cuda.synchronize()
+        _check(W.cpu().double().numpy(), H, V.double().numpy(), torch.float32)
         trbl.apply_set_compensated(th, True)
         for kern, rows, bps in SHAPES[1:]:
             trbl.apply_set_shape(th, kern, rows, bps)
@@ -305,7 +311,7 @@ def test_autotune_candidates_and_choice(medium):
     assert r == rows and kern in (trbl.TRBL_APPLY_GROUPED, trbl.TRBL_APPLY_FAST)
     assert torch.equal(th.apply(V).cpu(), ref)
     ms64, _ = trbl.apply_autotune(th, 16, trbl.TRBL_F64)
-    assert all(np.isfinite(ms64[:4])) and not any(np.isfinite(ms64[4:]))
+    assert all(np.isfinite(ms64[:4])) and not any(np.isfinite(ms64[4:10])) and all(np.isfinite(ms64[10:]))
     with pytest.raises(trbl.TrblError):
         trbl.apply_set_shape(th, 7, 16, 8)
     with pytest.raises(trbl.TrblError):
