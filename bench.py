@@ -748,6 +748,38 @@ def run_proj_only(args):
     print(json.dumps(out), flush=True)
 
 
+def run_wide_only(args):
+    """Time the wide tensor-core GEMM alone (the thick restart's V U and the
+    Ritz vectors; Out = In U, FP32 In and Out, FP64 U) for "D,K,n": FLOP
+    rate (2 D K n, three split TF32 products counted once) and bytes
+    4 D (K + n) against the measured peaks."""
+    import torch
+    import paper_1902_02064_gb300 as trbl
+    D, K, n = (int(x) for x in args.wide_only.split(","))
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    In = torch.rand((D, K), generator=g, device="cuda") * 2 - 1
+    U = (torch.rand((K, n), generator=g, device="cuda", dtype=torch.float64) * 2 - 1) / K
+    Out = torch.empty((D, (n + 3) // 4 * 4), device="cuda")[:, :n]
+    for _ in range(args.warmup):
+        trbl.block_update(In, U, Out, 1.0, 0.0, algo=trbl.TRBL_PROJ_TENSOR)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        trbl.block_update(In, U, Out, 1.0, 0.0, algo=trbl.TRBL_PROJ_TENSOR)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    peaks = measured_peaks() or {}
+    tf = 2.0 * D * K * n / (ms * 1e-3) / 1e12
+    gbs = 4.0 * D * (K + n) / (ms * 1e-3) / 1e9
+    print(json.dumps({"D": D, "K": K, "n": n, "ms": ms, "tflops_fp32_products": tf,
+                      "tf32_tflops_issued": 3 * tf, "gbs": gbs,
+                      "frac_hbm": gbs / peaks["hbm_gbs"] if peaks else None}), flush=True)
+
+
 def run_apply_only(args):
     """Time the block product alone on one workload (used for kernel profiles)."""
     import torch
@@ -798,8 +830,8 @@ def run_apply_only(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=8)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -814,6 +846,8 @@ def main():
                     help="only: time to nev eigenpairs at 1e-6 ||H|| on a large workload (s20_4p4n: mixed, "
                          "FP64 block and FP64 q = 1 arms; s20_5p5n: mixed) and print one JSON line")
     ap.add_argument("--apply-only", default=None, help="time only W = H V on this workload")
+    ap.add_argument("--wide-only", default=None, metavar="D,K,n",
+                    help="time only the wide tensor-core GEMM Out = In U (restart and Ritz vectors)")
     ap.add_argument("--proj-only", default=None, metavar="D,m,q",
                     help="time only the block projection and update (FP32, both forms) at these sizes")
     ap.add_argument("--workload", default=WORKLOAD, help="workload of the solver steps (default: the 5+5 space)")
@@ -832,6 +866,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.apply_only:
         run_apply_only(args)
+    elif args.wide_only:
+        run_wide_only(args)
     elif args.proj_only:
         run_proj_only(args)
     elif args.ttn_large:

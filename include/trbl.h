@@ -272,7 +272,23 @@ typedef struct trbl_params {
   double normH;        /* ||H|| used by tol; 0 = estimated by the solver (largest |Ritz value|) */
   int projections;     /* TRBL_PROJ_TENSOR (0, default) or TRBL_PROJ_CUDA_CORE: how the FP32
                           projections and updates of mixed precision are computed */
+  int reorth;          /* TRBL_REORTH_SELECTIVE (0, default) or TRBL_REORTH_TWICE (below) */
 } trbl_params;
+
+/* Reorthogonalisation of a block step (Sec. III C/D: the block is made
+ * orthogonal to every stored Lanczos vector).
+ * TRBL_REORTH_SELECTIVE: classical Gram-Schmidt against the last two blocks
+ *   (the three-term part of the recurrence, which carries W = H V_k's large
+ *   components), one full pass against every stored vector, and a second
+ *   full pass only in the steps where a column of the block lost more than
+ *   half its squared norm in the first (the Daniel-Gragg-Kaufman-Stewart
+ *   test; after a thick restart the couplings to the kept Ritz vectors make
+ *   the test fire).  One full pass removes what the first leaves when the
+ *   block was already orthogonal to the basis up to rounding.
+ * TRBL_REORTH_TWICE: two full passes every step (classical Gram-Schmidt
+ *   applied twice). */
+#define TRBL_REORTH_SELECTIVE 0
+#define TRBL_REORTH_TWICE 1
 
 /* Per-solve statistics (per-phase times mirror the paper's Fig. 5(c)). */
 typedef struct trbl_stats {
@@ -283,7 +299,7 @@ typedef struct trbl_stats {
   double normH;        /* ||H|| used by the tolerance */
   double ms_total, ms_apply, ms_orth, ms_qr, ms_ritz, ms_restart;
   int basis_size;      /* Lanczos vectors in the basis now (stepwise solver; the last step's for trbl_solve) */
-  int pad_;
+  int second_passes;   /* block steps that ran a second full reorthogonalisation pass */
 } trbl_stats;
 
 /* Lowest nev eigenpairs of H by the thick-restart block Lanczos method

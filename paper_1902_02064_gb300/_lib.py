@@ -13,6 +13,7 @@ TRBL_OK, TRBL_ERR_ARG, TRBL_ERR_CUDA, TRBL_ERR_OOM, TRBL_ERR_BREAKDOWN, TRBL_ERR
 TRBL_F32, TRBL_F64 = 0, 1
 TRBL_PREC_F64, TRBL_PREC_MIXED = 1, 2
 TRBL_PROJ_TENSOR, TRBL_PROJ_CUDA_CORE = 0, 1
+TRBL_REORTH_SELECTIVE, TRBL_REORTH_TWICE = 0, 1
 TRBL_NOALLOC_SCRATCH_BYTES = 8 << 20  # include/trbl.h
 TRBL_APPLY_GROUPED, TRBL_APPLY_FAST, TRBL_APPLY_GROUPED_X2 = 0, 1, 2
 TRBL_TUNE_CANDIDATES = 13
@@ -38,14 +39,14 @@ class trbl_params(C.Structure):
     _fields_ = [("nev", C.c_int), ("q", C.c_int), ("max_basis", C.c_int), ("keep", C.c_int),
                 ("tol", C.c_double), ("precision", C.c_int), ("max_iter", C.c_int),
                 ("check_every", C.c_int), ("seed", C.c_uint64), ("normH", C.c_double),
-                ("projections", C.c_int)]
+                ("projections", C.c_int), ("reorth", C.c_int)]
 
 
 class trbl_stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
                 ("status", C.c_int), ("normH", C.c_double), ("ms_total", C.c_double),
                 ("ms_apply", C.c_double), ("ms_orth", C.c_double), ("ms_qr", C.c_double),
-                ("ms_ritz", C.c_double), ("ms_restart", C.c_double), ("basis_size", C.c_int), ("pad_", C.c_int)]
+                ("ms_ritz", C.c_double), ("ms_restart", C.c_double), ("basis_size", C.c_int), ("second_passes", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -346,12 +347,12 @@ class Hamiltonian:
 def solve(h: Hamiltonian, nev: int, q: int, max_basis: int, tol: float,
           precision: int = TRBL_PREC_F64, keep: int = 0, max_iter: int = 0,
           check_every: int = 0, seed: int = 1, normH: float = 0.0, want_vectors: bool = True,
-          stream=None, raise_on_noconv: bool = True, projections: int = TRBL_PROJ_TENSOR):
+          stream=None, raise_on_noconv: bool = True, projections: int = TRBL_PROJ_TENSOR,
+          reorth: int = TRBL_REORTH_SELECTIVE):
     """Lowest nev eigenpairs by trbl_solve.  Returns (evals, resid, evecs or None, stats dict)."""
     import torch
     D = h.basis.dim
-    p = trbl_params(int(nev), int(q), int(max_basis), int(keep), float(tol), int(precision),
-                    int(max_iter), int(check_every), int(seed), float(normH), int(projections))
+    p = _params(nev, q, max_basis, tol, precision, keep, max_iter, check_every, seed, normH, projections, reorth)
     st = trbl_stats()
     ev = np.zeros(nev)
     rs = np.zeros(nev)
@@ -370,9 +371,9 @@ def solve(h: Hamiltonian, nev: int, q: int, max_basis: int, tol: float,
 
 
 def _params(nev, q, max_basis, tol, precision=TRBL_PREC_F64, keep=0, max_iter=0, check_every=0, seed=1,
-            normH=0.0, projections=TRBL_PROJ_TENSOR):
+            normH=0.0, projections=TRBL_PROJ_TENSOR, reorth=TRBL_REORTH_SELECTIVE):
     return trbl_params(int(nev), int(q), int(max_basis), int(keep), float(tol), int(precision),
-                       int(max_iter), int(check_every), int(seed), float(normH), int(projections))
+                       int(max_iter), int(check_every), int(seed), float(normH), int(projections), int(reorth))
 
 
 def trbl_solver_create(h: int, params: trbl_params, stream: int = 0) -> int:
@@ -477,7 +478,8 @@ class Solver:
 
     def __init__(self, h: Hamiltonian, nev: int, q: int, max_basis: int, tol: float,
                  precision: int = TRBL_PREC_F64, keep: int = 0, check_every: int = 0, seed: int = 1,
-                 normH: float = 0.0, stream=None, projections: int = TRBL_PROJ_TENSOR, max_iter: int = 0):
+                 normH: float = 0.0, stream=None, projections: int = TRBL_PROJ_TENSOR, max_iter: int = 0,
+                 reorth: int = TRBL_REORTH_SELECTIVE):
         import torch
         self.h = h
         self.nev, self.q, self.precision = nev, q, precision
@@ -485,7 +487,7 @@ class Solver:
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
         self.params = _params(nev, q, max_basis, tol, precision, keep, max_iter, check_every, seed, normH,
-                              projections)
+                              projections, reorth)
         self.handle = trbl_solver_create(h.handle, self.params, s.cuda_stream)
 
     def step(self) -> int:

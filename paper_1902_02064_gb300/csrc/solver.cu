@@ -140,6 +140,19 @@ __global__ void set_alpha_kernel(double* __restrict__ T, int ldt, const double* 
   T[int64_t(b0 + r) * ldt + b0 + c] = 0.5 * (C[(b0 + r) * q + c] + C[(b0 + c) * q + r]);
 }
 
+// C1[(b0 + i) q + j] = Cl[(q + i) q + j] + C[(b0 + i) q + j] (+ C2[...]): the
+// projection of H V_k onto V_k summed over the local and full passes
+__global__ void sum_alpha_kernel(double* __restrict__ C1, const double* __restrict__ Cl,
+                                 const double* __restrict__ C, const double* __restrict__ C2, int b0, int ql,
+                                 int q) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= q * q) return;
+  const int r = i / q, c = i - r * q;
+  double v = Cl[(ql - q + r) * q + c] + C[(b0 + r) * q + c];
+  if (C2) v += C2[(b0 + r) * q + c];
+  C1[(b0 + r) * q + c] = v;
+}
+
 // T[r0+i][c0+j] = beta[i][j], T[c0+j][r0+i] = beta[i][j]
 __global__ void set_beta_kernel(double* __restrict__ T, int ldt, const double* __restrict__ beta, int r0,
                                 int c0, int q) {
@@ -428,6 +441,8 @@ struct Solver {
   T *basis, *Vk, *W, *W2, *Wsave, *panel;
   int64_t panel_rows;
   double *C, *G, *R1, *R1i, *R2, *R2i, *beta, *Tm, *Aw, *theta, *Ut, *res, *syev_work, *Xd, *HXd, *rpart, *rtrue;
+  double *Cl, *Gn;  // local-pass coefficients (2q x q), block Gram matrices before / after the full pass
+  int second_passes = 0;
   int *flags, *devinfo;
   int lwork;
   int64_t nchunk_res;
@@ -459,6 +474,40 @@ struct Solver {
     TRY(rowgemm_ws<T>(basis, mb, nb, C, q, q, Wb, q, D, -1.0, 1.0, ws, s));
     TRY(block_dot<T>(basis, mb, nb, Wb, q, q, D, C + size_t(mb) * q, ws, s));
     TRY(rowgemm_ws<T>(basis, mb, nb, C + size_t(mb) * q, q, q, Wb, q, D, -1.0, 1.0, ws, s));
+    return TRBL_OK;
+  }
+
+  // Selective reorthogonalisation (TRBL_REORTH_SELECTIVE): classical
+  // Gram-Schmidt against the last two blocks (the three-term part of the
+  // recurrence), one full pass against all nb stored vectors, and a second
+  // full pass only when a column of W lost more than half its squared norm
+  // in the first (Daniel-Gragg-Kaufman-Stewart).  C1's rows nb-q .. nb
+  // receive the projection of W onto V_k summed over the passes.
+  int cgs_selective(T* Wb, int nb, double* C1) {
+    const int ql = std::min(2 * q, nb);
+    const T* Bl = basis + (nb - ql);
+    TRY(block_dot<T>(Bl, mb, ql, Wb, q, q, D, Cl, ws, s));
+    TRY(rowgemm_ws<T>(Bl, mb, ql, Cl, q, q, Wb, q, D, -1.0, 1.0, ws, s));
+    TRY(block_dot<T>(Wb, q, q, Wb, q, q, D, Gn, ws, s));
+    TRY(block_dot<T>(basis, mb, nb, Wb, q, q, D, C, ws, s));
+    TRY(rowgemm_ws<T>(basis, mb, nb, C, q, q, Wb, q, D, -1.0, 1.0, ws, s));
+    TRY(block_dot<T>(Wb, q, q, Wb, q, q, D, Gn + q * q, ws, s));
+    TRBL_CUDA(cudaMemcpyAsync(hbuf + 2 * mb, Gn, sizeof(double) * 2 * q * q, cudaMemcpyDeviceToHost, s));
+    TRBL_CUDA(cudaStreamSynchronize(s));
+    bool again = false;
+    for (int j = 0; j < q; ++j) {
+      const double before = hbuf[2 * mb + j * q + j], after = hbuf[2 * mb + q * q + j * q + j];
+      if (!(after > 0.5 * before)) again = true;  // also catches NaN and a vanished column
+    }
+    double* C2 = nullptr;
+    if (again) {
+      C2 = C + size_t(mb) * q;
+      TRY(block_dot<T>(basis, mb, nb, Wb, q, q, D, C2, ws, s));
+      TRY(rowgemm_ws<T>(basis, mb, nb, C2, q, q, Wb, q, D, -1.0, 1.0, ws, s));
+      ++second_passes;
+    }
+    sum_alpha_kernel<<<(q * q + 127) / 128, 128, 0, s>>>(C1, Cl, C, C2, nb - q, ql, q); note_launch();
+    TRBL_CUDA(cudaGetLastError());
     return TRBL_OK;
   }
 
@@ -666,7 +715,10 @@ struct Solver {
     TRY(apply(Vk, W));
     tm.rec(1, s);
     double* C1 = C + size_t(2) * mb * q;
-    TRY(cgs2(W, nb, C1));
+    if (p->reorth == TRBL_REORTH_TWICE)
+      TRY(cgs2(W, nb, C1));
+    else
+      TRY(cgs_selective(W, nb, C1));
     set_alpha_kernel<<<(q * q + 127) / 128, 128, 0, s>>>(Tm, mb, C1, nb - q, q); note_launch();
     TRBL_CUDA(cudaGetLastError());
     tm.rec(2, s);
@@ -795,6 +847,7 @@ struct Solver {
     st->ms_ritz = ms_ritz;
     st->ms_restart = ms_restart;
     st->basis_size = nb;
+    st->second_passes = second_passes;
   }
 
   // ---- checkpoint: the state between block steps ----
@@ -958,6 +1011,8 @@ struct Solver {
     if (h->row_end >= 0 && (h->row_begin != 0 || h->row_end != D))
       return fail(TRBL_ERR_ARG, "the solver needs the product over all rows (trbl_hamiltonian_set_rows(h, 0, D))");
     if (nev < 1) return fail(TRBL_ERR_ARG, "nev must be positive");
+    if (p->reorth != TRBL_REORTH_SELECTIVE && p->reorth != TRBL_REORTH_TWICE)
+      return fail(TRBL_ERR_ARG, "reorth must be TRBL_REORTH_SELECTIVE or TRBL_REORTH_TWICE");
     if (mb > D) return fail(TRBL_ERR_ARG, "max_basis=%d exceeds the dimension %lld", mb, (long long)D);
     if (mb < nev + 2 * q) return fail(TRBL_ERR_ARG, "max_basis must be at least nev + 2q");
     if (!(p->tol > 0.0)) return fail(TRBL_ERR_ARG, "tol must be positive");
@@ -986,6 +1041,8 @@ struct Solver {
       Wsave = ar.take<T>(dq);
       panel = ar.take<T>(size_t(panel_rows) * ((ls + 7) / 8 * 8));
       C = ar.take<double>(size_t(3) * mb * q);
+      Cl = ar.take<double>(size_t(2) * q * q);
+      Gn = ar.take<double>(size_t(2) * q * q);
       G = ar.take<double>(q * q);
       R1 = ar.take<double>(q * q);
       R1i = ar.take<double>(q * q);
@@ -1039,7 +1096,7 @@ struct Solver {
       }
     }
     TRBL_CUDA(cudaMemsetAsync(Tm, 0, sizeof(double) * mb * mb, s));
-    const size_t nh = size_t(2) * mb + size_t(q) * q;  // Ritz values, residuals / a q x q Gram
+    const size_t nh = size_t(2) * mb + size_t(2) * q * q;  // Ritz values, residuals / two q x q Gram matrices
     TRBL_CUDA(cudaMallocHost(&hbuf, sizeof(double) * nh + sizeof(int) * kFlagInts));
     hflags = reinterpret_cast<int*>(hbuf + nh);
     // The eigensolver loads size-dependent kernel variants on first use,
