@@ -317,9 +317,9 @@ typedef struct trbl_stats {
 int trbl_solve(const trbl_hamiltonian* h, const trbl_params* p, double* evals, double* resid,
                void* evecs, trbl_stats* stats, void* stream);
 
-/* Batched form of trbl_solve for nset Hamiltonians built on one basis (for
- * example many parameter sets of one model space), all with the same
- * parameters p.  One persistent launch of the block product serves every
+/* Batched form of trbl_solve for nset Hamiltonians (for example many
+ * parameter sets of one model space, or sectors of uneven dimension), all
+ * with the same parameters p (max_basis at most the smallest dimension).  One persistent launch of the block product serves every
  * set, and each other operation of a block step is one launch over all
  * sets; the step is captured into a CUDA graph per basis size and replayed
  * on a private stream.  Rayleigh-Ritz tests and restarts run
@@ -327,8 +327,12 @@ int trbl_solve(const trbl_hamiltonian* h, const trbl_params* p, double* evals, d
  * sets testing at the same steps.  stats: iterations = block steps, ms_total
  * = wall time of the whole call, ms_apply = wall time of the batched block
  * steps (product, orthogonalisation, QR of every set), ms_ritz = wall time
- * of the tests and restarts between them.  Outputs are set-major: evals and resid [nset * nev] (host),
- * evecs [nset][D x nev] (device, may be NULL), status [nset] (host, per-set
+ * of the tests and restarts between them.  The Hamiltonians may live on one
+ * basis (parameter sets) or on bases of different dimension (sectors of
+ * other 2M or particle numbers): each set keeps its own tables, work list
+ * and dimension D_s, and each batched launch covers all sets.  Outputs are
+ * set-major: evals and resid [nset * nev] (host), evecs (device, may be
+ * NULL) the sets' D_s x nev blocks one after another, status [nset] (host, per-set
  * return code, may be NULL); stats summarises the batch.  Needs
  * q * element size = 16 * 2^i bytes.  A rank-deficient block stops its set
  * with TRBL_ERR_BREAKDOWN (the column-wise repair of trbl_solve is not

@@ -677,26 +677,33 @@ def solve_batch(hs, nev: int, q: int, max_basis: int, tol: float, precision: int
                 keep: int = 0, max_iter: int = 0, check_every: int = 0, seed: int = 1, normH: float = 0.0,
                 want_vectors: bool = False, want_resid: bool = True, stream=None,
                 projections: int = TRBL_PROJ_TENSOR):
-    """trbl_solve_batch over Hamiltonians sharing one basis.  Returns
-    (evals [nset, nev], resid [nset, nev] or None, vectors [nset, D, nev] or
-    None, per-set status, stats dict)."""
+    """trbl_solve_batch over Hamiltonians on one basis or on bases of
+    different dimension.  Returns (evals [nset, nev], resid [nset, nev] or
+    None, vectors or None, per-set status, stats dict); vectors is a
+    [nset, D, nev] tensor when every set has the same dimension, else a list
+    of [D_s, nev] views (set-major in one buffer)."""
     import torch
     nset = len(hs)
-    D = hs[0].basis.dim
+    dims = [h.basis.dim for h in hs]
     p = _params(nev, q, max_basis, tol, precision, keep, max_iter, check_every, seed, normH, projections)
     arr = (_VP * nset)(*[h.handle for h in hs])
     ev = np.zeros((nset, nev))
     rs = np.zeros((nset, nev)) if want_resid else None
     status = (C.c_int * nset)()
-    X = None
+    X = buf = None
     if want_vectors:
         dt = torch.float64 if precision == TRBL_PREC_F64 else torch.float32
-        X = torch.empty((nset, D, nev), dtype=dt, device="cuda")
+        buf = torch.empty(sum(dims) * nev, dtype=dt, device="cuda")
+        if len(set(dims)) == 1:
+            X = buf.view(nset, dims[0], nev)
+        else:
+            offs = np.concatenate([[0], np.cumsum(dims)]) * nev
+            X = [buf[offs[i]:offs[i + 1]].view(dims[i], nev) for i in range(nset)]
     st = trbl_stats()
     s = stream if stream is not None else torch.cuda.current_stream()
     rc = lib().trbl_solve_batch(arr, nset, C.byref(p), ev.ctypes.data_as(_DP),
                                 rs.ctypes.data_as(_DP) if rs is not None else None,
-                                X.data_ptr() if X is not None else None, status, C.byref(st), s.cuda_stream)
+                                buf.data_ptr() if buf is not None else None, status, C.byref(st), s.cuda_stream)
     d = st.as_dict()
     d["rc"] = rc
     d["message"] = trbl_last_error() if rc else ""

@@ -275,16 +275,17 @@ __global__ void __launch_bounds__(kThreads, MINB)
   fast_body<LPE, COMP>(h, g, blockIdx.x, V, ld, W, ldw);
 }
 
-// Several Hamiltonians on one basis: blockIdx.y selects the set; set s reads
-// V + s * sv and writes W + s * sw.
+// Several Hamiltonians, on one basis or on bases of different dimension:
+// blockIdx.y selects the set, which reads Vs[set] and writes Ws[set]; a set
+// with fewer work items than the grid leaves the rest idle.
 template <int LPE, int MINB, bool COMP>
 __global__ void __launch_bounds__(kThreads, MINB)
     apply_fast_batch_kernel(const DevH<float>* __restrict__ hs, const DevG<float>* __restrict__ gs,
-                            const float* __restrict__ V, int ld, int64_t sv, float* __restrict__ W, int64_t ldw,
-                            int64_t sw) {
+                            const float* const* __restrict__ Vs, int ld, float* const* __restrict__ Ws, int64_t ldw) {
+  if (int(blockIdx.x) >= gs[blockIdx.y].nwork) return;
   const DevH<float> h = hs[blockIdx.y];
   const DevG<float> g = gs[blockIdx.y];
-  fast_body<LPE, COMP>(h, g, blockIdx.x, V + blockIdx.y * sv, ld, W + blockIdx.y * sw, ldw);
+  fast_body<LPE, COMP>(h, g, blockIdx.x, Vs[blockIdx.y], ld, Ws[blockIdx.y], ldw);
 }
 
 size_t fast_smem(const DevG<float>& g) {
@@ -306,14 +307,14 @@ int launch_lpe(const DevH<float>& h, const DevG<float>& g, const float* V, int l
 }
 
 template <int LPE, int MINB, bool COMP>
-int launch_batch_lpe(const DevH<float>* hs, const DevG<float>* gs, int nset, int nwork, size_t sm, const float* V,
-                     int ld, int64_t sv, float* W, int64_t ldw, int64_t sw, cudaStream_t s) {
+int launch_batch_lpe(const DevH<float>* hs, const DevG<float>* gs, int nset, int nwork, size_t sm,
+                     const float* const* V, int ld, float* const* W, int64_t ldw, cudaStream_t s) {
   static const cudaError_t cfg = cudaFuncSetAttribute(apply_fast_batch_kernel<LPE, MINB, COMP>,
                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
   TRBL_CUDA(cfg);
   if (sm > size_t(kMaxSmem)) return fail(TRBL_ERR_ARG, "product needs %zu bytes of shared memory", sm);
   const dim3 grid{static_cast<unsigned>(nwork), static_cast<unsigned>(nset), 1u};
-  apply_fast_batch_kernel<LPE, MINB, COMP><<<grid, kThreads, sm, s>>>(hs, gs, V, ld, sv, W, ldw, sw);
+  apply_fast_batch_kernel<LPE, MINB, COMP><<<grid, kThreads, sm, s>>>(hs, gs, V, ld, W, ldw);
   note_launch();
   TRBL_CUDA(cudaGetLastError());
   return TRBL_OK;
@@ -322,11 +323,9 @@ int launch_batch_lpe(const DevH<float>* hs, const DevG<float>* gs, int nset, int
 // Whether the fast kernel takes this call: FP32 rows of 32, 64 or 128 bytes,
 // 16-byte aligned, at most 31 transfer classes, 32-bit element offsets.
 bool fast_ok(const trbl_hamiltonian* h, const void* V, int64_t ldv, const void* W, int64_t ldw, int q) {
-  if (!h->g32.likeB || h->g32.nwork == 0 || h->b->ND > 31) return false;
-  if (q != 8 && q != 16 && q != 32) return false;
+  if (!fast_tables_ok(h, ldv, q)) return false;
   if ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(W)) & 15) return false;
-  if (ldv % 4 || ldw % 4 || ldv < q || ldw < q) return false;
-  if (h->b->D * ldv >= (int64_t(1) << 31)) return false;
+  if (ldw % 4 || ldw < q) return false;
   return true;
 }
 
@@ -342,14 +341,13 @@ int launch_q(const trbl_hamiltonian* h, const float* v, int ld, float* w, int64_
 
 template <int LPE>
 int launch_batch_q(const trbl_hamiltonian* h0, const DevH<float>* hs, const DevG<float>* gs, int nset, int nwork,
-                   size_t smem, const float* v, int ld, int64_t sv, float* w, int64_t ldw, int64_t sw,
-                   cudaStream_t s) {
+                   size_t smem, const float* const* v, int ld, float* const* w, int64_t ldw, cudaStream_t s) {
   const bool b6 = h0->blocks_per_sm == 6;
   if (h0->apply_compensated)
-    return b6 ? launch_batch_lpe<LPE, 6, true>(hs, gs, nset, nwork, smem, v, ld, sv, w, ldw, sw, s)
-              : launch_batch_lpe<LPE, 8, true>(hs, gs, nset, nwork, smem, v, ld, sv, w, ldw, sw, s);
-  return b6 ? launch_batch_lpe<LPE, 6, false>(hs, gs, nset, nwork, smem, v, ld, sv, w, ldw, sw, s)
-            : launch_batch_lpe<LPE, 8, false>(hs, gs, nset, nwork, smem, v, ld, sv, w, ldw, sw, s);
+    return b6 ? launch_batch_lpe<LPE, 6, true>(hs, gs, nset, nwork, smem, v, ld, w, ldw, s)
+              : launch_batch_lpe<LPE, 8, true>(hs, gs, nset, nwork, smem, v, ld, w, ldw, s);
+  return b6 ? launch_batch_lpe<LPE, 6, false>(hs, gs, nset, nwork, smem, v, ld, w, ldw, s)
+            : launch_batch_lpe<LPE, 8, false>(hs, gs, nset, nwork, smem, v, ld, w, ldw, s);
 }
 
 }  // namespace
@@ -369,20 +367,26 @@ int launch_fast(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, 
 
 size_t fast_smem_bytes(const trbl_hamiltonian* h) { return fast_smem(h->g32); }
 
-int launch_fast_batch(const trbl_hamiltonian* h0, const void* hs_dev, const void* gs_dev, int nset, int nwork,
-                      size_t smem, const void* V, int64_t ldv, int64_t sv, void* W, int64_t ldw, int64_t sw, int q,
+bool fast_tables_ok(const trbl_hamiltonian* h, int64_t ld, int q) {
+  if (!h->g32.likeB || h->g32.nwork == 0 || h->b->ND > 31) return false;
+  if (q != 8 && q != 16 && q != 32) return false;
+  if (ld % 4 || ld < q) return false;
+  return h->b->D * ld < (int64_t(1) << 31);
+}
+
+int launch_fast_batch(const trbl_hamiltonian* h0, bool all, const void* hs_dev, const void* gs_dev, int nset,
+                      int nwork, size_t smem, const void* Vs, int64_t ldv, const void* Ws, int64_t ldw, int q,
                       cudaStream_t s) {
-  if (h0->apply_kernel != TRBL_APPLY_FAST || !fast_ok(h0, V, ldv, W, ldw, q)) return -1;
-  if ((sv | sw) % 4) return -1;
+  if (!all || h0->apply_kernel != TRBL_APPLY_FAST || !fast_tables_ok(h0, ldv, q) || ldw % 4 || ldw < q) return -1;
   const auto* hs = static_cast<const DevH<float>*>(hs_dev);
   const auto* gs = static_cast<const DevG<float>*>(gs_dev);
-  const float* v = static_cast<const float*>(V);
-  float* w = static_cast<float*>(W);
+  const auto* v = static_cast<const float* const*>(Vs);
+  auto* w = static_cast<float* const*>(const_cast<void*>(Ws));
   const int ld = int(ldv);
   switch (q) {
-    case 8: return launch_batch_q<2>(h0, hs, gs, nset, nwork, smem, v, ld, sv, w, ldw, sw, s);
-    case 16: return launch_batch_q<4>(h0, hs, gs, nset, nwork, smem, v, ld, sv, w, ldw, sw, s);
-    default: return launch_batch_q<8>(h0, hs, gs, nset, nwork, smem, v, ld, sv, w, ldw, sw, s);
+    case 8: return launch_batch_q<2>(h0, hs, gs, nset, nwork, smem, v, ld, w, ldw, s);
+    case 16: return launch_batch_q<4>(h0, hs, gs, nset, nwork, smem, v, ld, w, ldw, s);
+    default: return launch_batch_q<8>(h0, hs, gs, nset, nwork, smem, v, ld, w, ldw, s);
   }
 }
 

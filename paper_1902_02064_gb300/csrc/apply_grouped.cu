@@ -239,16 +239,18 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T, CPL>::value) apply_grou
   grouped_body<T, LPE, CPL>(h, g, blockIdx.x, V, ldv, W, ldw);
 }
 
-// Several Hamiltonians on one basis: blockIdx.y selects the set; set s reads
-// V + s * sv and writes W + s * sw.
+// Several Hamiltonians, on one basis or on bases of different dimension:
+// blockIdx.y selects the set, which reads Vs[set] and writes Ws[set];
+// blockIdx.x runs over the largest work list and a set with fewer work
+// items leaves the rest idle.
 template <typename T, int LPE, int CPL>
-__global__ void __launch_bounds__(kThreads, MinBlocks<T, CPL>::value) apply_grouped_batch_kernel(const DevH<T>* __restrict__ hs,
-                                                                       const DevG<T>* __restrict__ gs,
-                                                                       const T* __restrict__ V, int64_t ldv, int64_t sv,
-                                                                       T* __restrict__ W, int64_t ldw, int64_t sw) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<T, CPL>::value)
+    apply_grouped_batch_kernel(const DevH<T>* __restrict__ hs, const DevG<T>* __restrict__ gs,
+                               const T* const* __restrict__ Vs, int64_t ldv, T* const* __restrict__ Ws, int64_t ldw) {
+  if (int(blockIdx.x) >= gs[blockIdx.y].nwork) return;
   const DevH<T> h = hs[blockIdx.y];
   const DevG<T> g = gs[blockIdx.y];
-  grouped_body<T, LPE, CPL>(h, g, blockIdx.x, V + blockIdx.y * sv, ldv, W + blockIdx.y * sw, ldw);
+  grouped_body<T, LPE, CPL>(h, g, blockIdx.x, Vs[blockIdx.y], ldv, Ws[blockIdx.y], ldw);
 }
 
 size_t smem_bytes(int maxP, int maxQ, int maxK, int ND, size_t tsize) {
@@ -295,28 +297,28 @@ int launch_typed(const trbl_hamiltonian* hm, const DevH<T>& h, const DevG<T>& g,
 }
 
 template <typename T, int LPE, int CPL>
-int launch_batch_lpe(const DevH<T>* hs, const DevG<T>* gs, int nset, int nwork, size_t sm, const T* V, int64_t ldv,
-                     int64_t sv, T* W, int64_t ldw, int64_t sw, cudaStream_t s) {
+int launch_batch_lpe(const DevH<T>* hs, const DevG<T>* gs, int nset, int nwork, size_t sm, const T* const* V,
+                     int64_t ldv, T* const* W, int64_t ldw, cudaStream_t s) {
   static const cudaError_t cfg = cudaFuncSetAttribute(apply_grouped_batch_kernel<T, LPE, CPL>,
                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
   TRBL_CUDA(cfg);
   if (sm > size_t(kMaxSmem)) return fail(TRBL_ERR_ARG, "product needs %zu bytes of shared memory", sm);
   const dim3 grid{static_cast<unsigned>(nwork), static_cast<unsigned>(nset), 1u};
-  apply_grouped_batch_kernel<T, LPE, CPL><<<grid, kThreads, sm, s>>>(hs, gs, V, ldv, sv, W, ldw, sw); note_launch();
+  apply_grouped_batch_kernel<T, LPE, CPL><<<grid, kThreads, sm, s>>>(hs, gs, V, ldv, W, ldw); note_launch();
   TRBL_CUDA(cudaGetLastError());
   return TRBL_OK;
 }
 
 template <typename T>
-int batch_typed(const DevH<T>* hs, const DevG<T>* gs, int nset, int nwork, size_t sm, const T* V, int64_t ldv,
-                int64_t sv, T* W, int64_t ldw, int64_t sw, int q, cudaStream_t s) {
+int batch_typed(const DevH<T>* hs, const DevG<T>* gs, int nset, int nwork, size_t sm, const T* const* V, int64_t ldv,
+                T* const* W, int64_t ldw, int q, cudaStream_t s) {
   switch (q * int(sizeof(T)) / 16) {
-    case 1: return launch_batch_lpe<T, 1, 1>(hs, gs, nset, nwork, sm, V, ldv, sv, W, ldw, sw, s);
-    case 2: return launch_batch_lpe<T, 2, 1>(hs, gs, nset, nwork, sm, V, ldv, sv, W, ldw, sw, s);
-    case 4: return launch_batch_lpe<T, 4, 1>(hs, gs, nset, nwork, sm, V, ldv, sv, W, ldw, sw, s);
-    case 8: return launch_batch_lpe<T, 8, 1>(hs, gs, nset, nwork, sm, V, ldv, sv, W, ldw, sw, s);
-    case 16: return launch_batch_lpe<T, 4, 4>(hs, gs, nset, nwork, sm, V, ldv, sv, W, ldw, sw, s);
-    case 32: return launch_batch_lpe<T, 4, 8>(hs, gs, nset, nwork, sm, V, ldv, sv, W, ldw, sw, s);
+    case 1: return launch_batch_lpe<T, 1, 1>(hs, gs, nset, nwork, sm, V, ldv, W, ldw, s);
+    case 2: return launch_batch_lpe<T, 2, 1>(hs, gs, nset, nwork, sm, V, ldv, W, ldw, s);
+    case 4: return launch_batch_lpe<T, 4, 1>(hs, gs, nset, nwork, sm, V, ldv, W, ldw, s);
+    case 8: return launch_batch_lpe<T, 8, 1>(hs, gs, nset, nwork, sm, V, ldv, W, ldw, s);
+    case 16: return launch_batch_lpe<T, 4, 4>(hs, gs, nset, nwork, sm, V, ldv, W, ldw, s);
+    case 32: return launch_batch_lpe<T, 4, 8>(hs, gs, nset, nwork, sm, V, ldv, W, ldw, s);
     default: return fail(TRBL_ERR_ARG, "batched product: q * element size must be 16 * 2^i bytes (<= 512)");
   }
 }
@@ -328,14 +330,15 @@ size_t grouped_smem_bytes(const trbl_hamiltonian* h, int dtype) {
   return smem_bytes(g.maxP, g.maxQ, g.maxK, h->b->ND, dtype == TRBL_F64 ? 8 : 4);
 }
 
-int launch_grouped_batch(const void* hs_dev, const void* gs_dev, int nset, int nwork, size_t smem, const void* V,
-                         int64_t ldv, int64_t sv, void* W, int64_t ldw, int64_t sw, int q, int dtype, cudaStream_t s) {
+int launch_grouped_batch(const void* hs_dev, const void* gs_dev, int nset, int nwork, size_t smem, const void* Vs,
+                         int64_t ldv, const void* Ws, int64_t ldw, int q, int dtype, cudaStream_t s) {
   if (dtype == TRBL_F64)
     return batch_typed<double>(static_cast<const DevH<double>*>(hs_dev), static_cast<const DevG<double>*>(gs_dev),
-                               nset, nwork, smem, static_cast<const double*>(V), ldv, sv, static_cast<double*>(W),
-                               ldw, sw, q, s);
+                               nset, nwork, smem, static_cast<const double* const*>(Vs), ldv,
+                               static_cast<double* const*>(const_cast<void*>(Ws)), ldw, q, s);
   return batch_typed<float>(static_cast<const DevH<float>*>(hs_dev), static_cast<const DevG<float>*>(gs_dev), nset,
-                            nwork, smem, static_cast<const float*>(V), ldv, sv, static_cast<float*>(W), ldw, sw, q, s);
+                            nwork, smem, static_cast<const float* const*>(Vs), ldv,
+                            static_cast<float* const*>(const_cast<void*>(Ws)), ldw, q, s);
 }
 
 int launch_grouped(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, int64_t ldw, int q, int dtype,

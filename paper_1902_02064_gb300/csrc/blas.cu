@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(32 * (QP / 4)) block_dot_kernel(
 template <typename T, int QP>
 __global__ void __launch_bounds__(32 * (QP / 4)) block_dot_batched_kernel(
     const T* const* __restrict__ Bs_, int64_t ldb, int m, const T* const* __restrict__ Ws_, int64_t ldw, int q,
-    int64_t D, int64_t rows_per_chunk, double* const* __restrict__ partials) {
+    const int64_t* __restrict__ Ds, int64_t rows_per_chunk, double* const* __restrict__ partials) {
+  const int64_t D = Ds[blockIdx.z];
   const T* __restrict__ B = Bs_[blockIdx.z];
   const T* __restrict__ W = Ws_[blockIdx.z];
   double* __restrict__ partial = partials[blockIdx.z];
@@ -244,7 +245,9 @@ __global__ void __launch_bounds__(RT * CT / 16) rowgemm_kernel(
 template <typename T, int RT, int CT>
 __global__ void __launch_bounds__(RT * CT / 16) rowgemm_batched_kernel(
     const T* const* __restrict__ Ins, int64_t ldi, int K, const double* const* __restrict__ Us_, int64_t ldu, int n,
-    T* const* __restrict__ Outs, int64_t ldo, int64_t D, double alpha, double beta) {
+    T* const* __restrict__ Outs, int64_t ldo, const int64_t* __restrict__ Ds, double alpha, double beta) {
+  const int64_t D = Ds[blockIdx.z];
+  if (int64_t(blockIdx.x) * RT >= D) return;
   const T* __restrict__ In = Ins[blockIdx.z];
   const double* __restrict__ U = Us_[blockIdx.z];
   T* __restrict__ Out = Outs[blockIdx.z];
@@ -604,8 +607,9 @@ void reduce_partials(const double* partial, int nchunk, int mq, double* C, cudaS
 }
 
 template <typename T>
-int block_dot_batched(const T* const* B, int64_t ldb, int m, const T* const* W, int64_t ldw, int q, int64_t D,
-                      double* const* C, double* const* partial, size_t partial_bytes, int nset, cudaStream_t s) {
+int block_dot_batched(const T* const* B, int64_t ldb, int m, const T* const* W, int64_t ldw, int q,
+                      const int64_t* Ds, int64_t D, double* const* C, double* const* partial, size_t partial_bytes,
+                      int nset, cudaStream_t s) {
   if (m <= 0 || nset <= 0 || D <= 0) return TRBL_OK;
   constexpr int RS = DotCfg<T>::RS;
   const int mtiles = (m + MT - 1) / MT;
@@ -619,7 +623,7 @@ int block_dot_batched(const T* const* B, int64_t ldb, int m, const T* const* W, 
   nchunk = (D + rows - 1) / rows;
   const dim3 grid{unsigned(mtiles), unsigned(nchunk), unsigned(nset)};
 #define TRBL_BDOT(QP) \
-  block_dot_batched_kernel<T, QP><<<grid, 32 * (QP / 4), 0, s>>>(B, ldb, m, W, ldw, q, D, rows, partial)
+  block_dot_batched_kernel<T, QP><<<grid, 32 * (QP / 4), 0, s>>>(B, ldb, m, W, ldw, q, Ds, rows, partial)
   if (q <= 4) TRBL_BDOT(4);
   else if (q <= 8) TRBL_BDOT(8);
   else if (q <= 16) TRBL_BDOT(16);
@@ -638,34 +642,39 @@ int block_dot_batched(const T* const* B, int64_t ldb, int m, const T* const* W, 
 
 template <typename T>
 int rowgemm_batched(const T* const* In, int64_t ldi, int K, const double* const* U, int64_t ldu, int n,
-                    T* const* Out, int64_t ldo, int64_t D, double alpha, double beta, int nset, cudaStream_t s) {
+                    T* const* Out, int64_t ldo, const int64_t* Ds, int64_t D, double alpha, double beta, int nset,
+                    cudaStream_t s) {
   if (n <= 0 || D <= 0 || K <= 0 || nset <= 0) return TRBL_OK;
   if (n <= 16) {
     constexpr int RT = 128, CT = 16;
     const dim3 grid{unsigned((D + RT - 1) / RT), unsigned((n + CT - 1) / CT), unsigned(nset)};
-    rowgemm_batched_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta);
+    rowgemm_batched_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, Ds, alpha, beta);
   } else if (n <= 32) {
     constexpr int RT = 128, CT = 32;
     const dim3 grid{unsigned((D + RT - 1) / RT), unsigned((n + CT - 1) / CT), unsigned(nset)};
-    rowgemm_batched_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta);
+    rowgemm_batched_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, Ds, alpha, beta);
   } else {
     constexpr int RT = 64, CT = 64;
     const dim3 grid{unsigned((D + RT - 1) / RT), unsigned((n + CT - 1) / CT), unsigned(nset)};
-    rowgemm_batched_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta);
+    rowgemm_batched_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, Ds, alpha, beta);
   }
   note_launch();
   TRBL_CUDA(cudaGetLastError());
   return TRBL_OK;
 }
 
-template int block_dot_batched<float>(const float* const*, int64_t, int, const float* const*, int64_t, int, int64_t,
-                                      double* const*, double* const*, size_t, int, cudaStream_t);
+template int block_dot_batched<float>(const float* const*, int64_t, int, const float* const*, int64_t, int,
+                                      const int64_t*, int64_t, double* const*, double* const*, size_t, int,
+                                      cudaStream_t);
 template int block_dot_batched<double>(const double* const*, int64_t, int, const double* const*, int64_t, int,
-                                       int64_t, double* const*, double* const*, size_t, int, cudaStream_t);
+                                       const int64_t*, int64_t, double* const*, double* const*, size_t, int,
+                                       cudaStream_t);
 template int rowgemm_batched<float>(const float* const*, int64_t, int, const double* const*, int64_t, int,
-                                    float* const*, int64_t, int64_t, double, double, int, cudaStream_t);
+                                    float* const*, int64_t, const int64_t*, int64_t, double, double, int,
+                                    cudaStream_t);
 template int rowgemm_batched<double>(const double* const*, int64_t, int, const double* const*, int64_t, int,
-                                     double* const*, int64_t, int64_t, double, double, int, cudaStream_t);
+                                     double* const*, int64_t, const int64_t*, int64_t, double, double, int,
+                                     cudaStream_t);
 
 template <typename T>
 int block_dot_capped(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, int64_t D, double* C,

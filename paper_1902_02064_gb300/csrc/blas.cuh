@@ -82,16 +82,19 @@ int gemm_wide_tc(const float* In, int64_t ldi, int K, const double* U, int64_t l
 // Enqueues a copy of the wide GEMM's wait-timeout word to host memory.
 int wide_error_to_host(int* host, cudaStream_t s);
 
-// Batched forms for nset problems of equal shapes, one launch each (plus the
-// reduction): problem s reads and writes through the s-th entry of device
-// arrays of pointers.  block_dot_batched uses about 1,024 rows per thread
-// block so that many small problems fill the GPU together.
+// Batched forms for nset problems of equal column shapes, one launch each
+// (plus the reduction): problem s reads and writes through the s-th entry of
+// device arrays of pointers and has Ds[s] rows (device array; D = the
+// largest, which sizes the grid).  block_dot_batched uses about 1,024 rows
+// per thread block so that many small problems fill the GPU together.
 template <typename T>
-int block_dot_batched(const T* const* B, int64_t ldb, int m, const T* const* W, int64_t ldw, int q, int64_t D,
-                      double* const* C, double* const* partial, size_t partial_bytes, int nset, cudaStream_t s);
+int block_dot_batched(const T* const* B, int64_t ldb, int m, const T* const* W, int64_t ldw, int q,
+                      const int64_t* Ds, int64_t D, double* const* C, double* const* partial, size_t partial_bytes,
+                      int nset, cudaStream_t s);
 template <typename T>
 int rowgemm_batched(const T* const* In, int64_t ldi, int K, const double* const* U, int64_t ldu, int n,
-                    T* const* Out, int64_t ldo, int64_t D, double alpha, double beta, int nset, cudaStream_t s);
+                    T* const* Out, int64_t ldo, const int64_t* Ds, int64_t D, double alpha, double beta, int nset,
+                    cudaStream_t s);
 
 // dst[:, 0:ncol] = src[:, 0:ncol] (with type conversion).
 template <typename S, typename T>

@@ -144,9 +144,11 @@ bool is_slab_boundary(const trbl_basis* b, int64_t r);
 // Dynamic shared memory of the grouped kernel for one Hamiltonian.
 size_t grouped_smem_bytes(const trbl_hamiltonian* h, int dtype);
 // One launch of the grouped kernel over nset Hamiltonians (device arrays of
-// DevH<T> / DevG<T>), set s reading V + s*sv and writing W + s*sw.
-int launch_grouped_batch(const void* hs_dev, const void* gs_dev, int nset, int nwork, size_t smem, const void* V,
-                         int64_t ldv, int64_t sv, void* W, int64_t ldw, int64_t sw, int q, int dtype, cudaStream_t s);
+// DevH<T> / DevG<T>, possibly on bases of different dimension), set s
+// reading the device pointer Vs[s] and writing Ws[s]; nwork = the largest
+// work list.
+int launch_grouped_batch(const void* hs_dev, const void* gs_dev, int nset, int nwork, size_t smem, const void* Vs,
+                         int64_t ldv, const void* Ws, int64_t ldw, int q, int dtype, cudaStream_t s);
 // Enqueues W = H V with the grouped kernel when q and the alignment allow it;
 // returns -1 (nothing launched) otherwise.
 int launch_grouped(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, int64_t ldw, int q,
@@ -157,11 +159,14 @@ int launch_grouped(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* 
 int launch_fast(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, int64_t ldw, int q, int dtype,
                 cudaStream_t s);
 size_t fast_smem_bytes(const trbl_hamiltonian* h);
-// The fast product over nset Hamiltonians of h0's basis (device arrays of
-// DevH<float> / DevG<float>); -1 when it does not apply.
-int launch_fast_batch(const trbl_hamiltonian* h0, const void* hs_dev, const void* gs_dev, int nset, int nwork,
-                      size_t smem, const void* V, int64_t ldv, int64_t sv, void* W, int64_t ldw, int64_t sw, int q,
+// The fast product over nset Hamiltonians (device arrays of DevH<float> /
+// DevG<float> and of per-set V and W pointers); shape from h0; all = the
+// fast kernel applies to every set; -1 when it does not apply.
+int launch_fast_batch(const trbl_hamiltonian* h0, bool all, const void* hs_dev, const void* gs_dev, int nset,
+                      int nwork, size_t smem, const void* Vs, int64_t ldv, const void* Ws, int64_t ldw, int q,
                       cudaStream_t s);
+// Whether the fast kernel can take products of h with row strides ld.
+bool fast_tables_ok(const trbl_hamiltonian* h, int64_t ld, int q);
 // Enqueues W = H V (apply.cu).
 int launch_apply(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, int64_t ldw,
                  int q, int dtype, cudaStream_t s);

@@ -251,6 +251,7 @@ struct SetPtrs {
   double* Tm;
   int* flags;
   double thr1;  // absolute pivot threshold of the pass-1 Cholesky (tau ||H||)
+  int64_t D;    // the set's dimension
 };
 
 // block s = set s: the pass-1 (pass = 1) or pass-2 Cholesky of its Gram
@@ -350,12 +351,12 @@ __global__ void beta_batched_kernel(const SetPtrs<T>* __restrict__ sp, int ldt, 
   }
 }
 
-// grid (., sets): basis_s[:, col0 : col0 + q] = Vk_s
+// grid (., sets): basis_s[:, col0 : col0 + q] = Vk_s over the set's D rows
 template <typename T>
-__global__ void append_batched_kernel(const SetPtrs<T>* __restrict__ sp, int64_t D, int q, int ldb, int col0) {
+__global__ void append_batched_kernel(const SetPtrs<T>* __restrict__ sp, int q, int ldb, int col0) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= D * q) return;
   const SetPtrs<T> p = sp[blockIdx.y];
+  if (i >= p.D * q) return;
   const int64_t r = i / q;
   const int c = int(i - r * q);
   p.basis[r * ldb + col0 + c] = p.Vk[i];
@@ -1178,7 +1179,12 @@ struct BatchDriver {
   int nset = 0, nwork = 0, dtype = 0, device = 0, nthreads = 1;
   size_t smem = 0, smem_fast = 0;
   const trbl_hamiltonian* h0 = nullptr;  // the first set's Hamiltonian: launch shape of the batch's product
-  int64_t D = 0;
+  bool all_fast = false;                 // the FP32 fast product applies to every set
+  int64_t D = 0;                         // the largest set dimension (grid sizes)
+  std::vector<int64_t> Ds;               // each set's dimension
+  std::vector<size_t> voff;              // each set's V_k (and W) offset in the shared buffer, in elements
+  size_t vtotal = 0;                     // elements of all sets' V_k together
+  int64_t* P_D = nullptr;                // device copy of Ds
   int q = 0, mb = 0;
   void* shared = nullptr;  // V_k and W of all sets, set-major
   void* tables = nullptr;  // DevH<T>[nset], DevG<T>[nset]
@@ -1257,15 +1263,14 @@ struct BatchDriver {
   // Set i's setup and start block on its own stream.
   int setup_set(const trbl_hamiltonian* h, int i) {
     Solver<T>* S = sets[i];
-    const size_t dq = size_t(D) * q;
     T* V0 = static_cast<T*>(shared);
     S->h = h;
     S->p = &prm;
     S->s = ss[i];
     S->skip_warmup = i > 0;
     TRY(S->setup());
-    S->Vk = V0 + dq * i;
-    S->W = V0 + dq * nset + dq * i;
+    S->Vk = V0 + voff[i];
+    S->W = V0 + vtotal + voff[i];
     TRY(S->init());
     TRBL_CUDA(cudaEventRecord(ev_done[i], ss[i]));
     return TRBL_OK;
@@ -1273,24 +1278,38 @@ struct BatchDriver {
 
   int setup(const trbl_hamiltonian* const* hs) {
     t_start = clock::now();
-    const trbl_basis* b = hs[0]->b;
-    D = b->D;
     q = prm.q;
     mb = prm.max_basis;
     dtype = std::is_same<T, double>::value ? TRBL_F64 : TRBL_F32;
     const int bytes = q * int(sizeof(T));
     if (bytes % 16 || (bytes & (bytes - 1)) || bytes > 512)
       return fail(TRBL_ERR_ARG, "batched solve needs q * element size = 16 * 2^i bytes (<= 512)");
+    // sets may live on different bases (sectors of other 2M or particle
+    // numbers): each keeps its own dimension, tables and work list
+    all_fast = dtype == TRBL_F32;
+    Ds.assign(nset, 0);
+    voff.assign(nset, 0);
+    vtotal = 0;
+    nwork = 0;
     for (int i = 0; i < nset; ++i) {
-      if (!hs[i] || hs[i]->b != b) return fail(TRBL_ERR_ARG, "batched Hamiltonians must share one basis");
-      if (!hs[i]->garena) return fail(TRBL_ERR_ARG, "the grouped product is not available for this basis");
+      if (!hs[i]) return fail(TRBL_ERR_ARG, "null Hamiltonian in the batch (set %d)", i);
+      if (!hs[i]->garena) return fail(TRBL_ERR_ARG, "the grouped product is not available for the basis of set %d", i);
+      if (hs[i]->row_end >= 0 && (hs[i]->row_begin != 0 || hs[i]->row_end != hs[i]->b->D))
+        return fail(TRBL_ERR_ARG, "set %d: the solver needs the product over all rows", i);
       if (hs[i]->rows_per_item != hs[0]->rows_per_item)
         TRY(set_work_items(const_cast<trbl_hamiltonian*>(hs[i]), hs[0]->rows_per_item));
       smem = std::max(smem, grouped_smem_bytes(hs[i], dtype));
-      if (dtype == TRBL_F32) smem_fast = std::max(smem_fast, fast_smem_bytes(hs[i]));
+      if (dtype == TRBL_F32) {
+        smem_fast = std::max(smem_fast, fast_smem_bytes(hs[i]));
+        all_fast = all_fast && fast_tables_ok(hs[i], q, q);
+      }
+      Ds[i] = hs[i]->b->D;
+      voff[i] = vtotal;
+      vtotal += size_t(Ds[i]) * q;
+      D = std::max(D, Ds[i]);
+      nwork = std::max(nwork, hs[i]->g32.nwork);
     }
     h0 = hs[0];
-    nwork = hs[0]->g32.nwork;
     TRBL_CUDA(cudaGetDevice(&device));
     nthreads = int(std::max(1u, std::min(16u, std::thread::hardware_concurrency())));
     rc.assign(nset, TRBL_OK);
@@ -1301,8 +1320,7 @@ struct BatchDriver {
       TRBL_CUDA(cudaStreamCreateWithFlags(&ss[i], cudaStreamNonBlocking));
       TRBL_CUDA(cudaEventCreateWithFlags(&ev_done[i], cudaEventDisableTiming));
     }
-    const size_t dq = size_t(D) * q;
-    TRBL_CUDA(cudaMalloc(&shared, sizeof(T) * dq * 2 * nset));
+    TRBL_CUDA(cudaMalloc(&shared, sizeof(T) * vtotal * 2));
     TRBL_CUDA(cudaMalloc(&tables, (sizeof(DevH<T>) + sizeof(DevG<T>)) * nset));
     std::vector<DevH<T>> hv(nset);
     std::vector<DevG<T>> gv(nset);
@@ -1337,7 +1355,8 @@ struct BatchDriver {
   // Device arrays of the sets' pointers for the batched step.
   int setup_pointers() {
     const size_t np = size_t(nset);
-    const size_t bytes = np * (4 * sizeof(T*) + 6 * sizeof(double*)) + np * sizeof(SetPtrs<T>) + 2 * np * sizeof(int) + 256;
+    const size_t bytes = np * (4 * sizeof(T*) + 6 * sizeof(double*)) + np * sizeof(SetPtrs<T>) + 2 * np * sizeof(int) +
+                         np * sizeof(int64_t) + 512;
     TRBL_CUDA(cudaMalloc(&bptr, bytes));
     TRBL_CUDA(cudaMallocHost(&hsp, np * sizeof(SetPtrs<T>)));
     TRBL_CUDA(cudaMallocHost(&hcounts, (2 * np + 4) * sizeof(int)));
@@ -1364,9 +1383,13 @@ struct BatchDriver {
     dsp = reinterpret_cast<SetPtrs<T>*>(static_cast<char*>(bptr) + off);
     for (int i = 0; i < nset; ++i) {
       Solver<T>& S = *sets[i];
-      hsp[i] = SetPtrs<T>{S.basis, S.Vk, S.C, S.G, S.R1, S.R1i, S.R2, S.R2i, S.beta, S.Tm, S.flags, 0.0};
+      hsp[i] = SetPtrs<T>{S.basis, S.Vk, S.C, S.G, S.R1, S.R1i, S.R2, S.R2i, S.beta, S.Tm, S.flags, 0.0, Ds[i]};
     }
     off += np * sizeof(SetPtrs<T>);
+    off = (off + 15) & ~size_t(15);
+    P_D = reinterpret_cast<int64_t*>(static_cast<char*>(bptr) + off);
+    std::memcpy(host.data() + off, Ds.data(), np * sizeof(int64_t));
+    off += np * sizeof(int64_t);
     dcounts = reinterpret_cast<int*>(static_cast<char*>(bptr) + off);
     part_bytes = sets[0]->ws.partial_bytes;
     TRBL_CUDA(cudaMemcpy(bptr, host.data(), bytes, cudaMemcpyHostToDevice));
@@ -1378,38 +1401,34 @@ struct BatchDriver {
   // V_{k+1}, each a single launch over all sets; then the deficiency counts
   // and wait-timeout words to pinned host memory.
   int enqueue(bool append) {
-    T* V0 = static_cast<T*>(shared);
-    const size_t dq = size_t(D) * q;
     const void* gtab = static_cast<char*>(tables) + sizeof(DevH<T>) * nset;
     int rf = -1;
     if (dtype == TRBL_F32)
-      rf = launch_fast_batch(h0, tables, gtab, nset, nwork, smem_fast, V0, q, int64_t(dq), V0 + dq * nset, q,
-                             int64_t(dq), q, s);
+      rf = launch_fast_batch(h0, all_fast, tables, gtab, nset, nwork, smem_fast, P_Vk, q, P_W, q, q, s);
     if (rf == -1)
-      TRY(launch_grouped_batch(tables, gtab, nset, nwork, smem, V0, q, int64_t(dq), V0 + dq * nset, q, int64_t(dq), q,
-                               dtype, s));
+      TRY(launch_grouped_batch(tables, gtab, nset, nwork, smem, P_Vk, q, P_W, q, q, dtype, s));
     else if (rf != TRBL_OK)
       return rf;
     const int nb = sets[0]->nb;
     const T* const* cB = P_basis;
     const T* const* cW = P_W;
     const T* const* cW2 = P_W2;
-    TRY(block_dot_batched<T>(cB, mb, nb, cW, q, q, D, P_C1, P_part, part_bytes, nset, s));
-    TRY(rowgemm_batched<T>(cB, mb, nb, P_C1, q, q, P_W, q, D, -1.0, 1.0, nset, s));
-    TRY(block_dot_batched<T>(cB, mb, nb, cW, q, q, D, P_C2, P_part, part_bytes, nset, s));
-    TRY(rowgemm_batched<T>(cB, mb, nb, P_C2, q, q, P_W, q, D, -1.0, 1.0, nset, s));
+    TRY(block_dot_batched<T>(cB, mb, nb, cW, q, q, P_D, D, P_C1, P_part, part_bytes, nset, s));
+    TRY(rowgemm_batched<T>(cB, mb, nb, P_C1, q, q, P_W, q, P_D, D, -1.0, 1.0, nset, s));
+    TRY(block_dot_batched<T>(cB, mb, nb, cW, q, q, P_D, D, P_C2, P_part, part_bytes, nset, s));
+    TRY(rowgemm_batched<T>(cB, mb, nb, P_C2, q, q, P_W, q, P_D, D, -1.0, 1.0, nset, s));
     const dim3 gq{unsigned((q * q + 127) / 128), unsigned(nset), 1u};
     set_alpha_batched_kernel<T><<<gq, 128, 0, s>>>(dsp, mb, nb - q, q); note_launch();
-    TRY(block_dot_batched<T>(cW, q, q, cW, q, q, D, P_G, P_part, part_bytes, nset, s));
+    TRY(block_dot_batched<T>(cW, q, q, cW, q, q, P_D, D, P_G, P_part, part_bytes, nset, s));
     chol_batched_kernel<T><<<nset, 64, 0, s>>>(dsp, q, 1, 0.0, sets[0]->tau_max); note_launch();
-    TRY(rowgemm_batched<T>(cW, q, q, P_R1i, q, q, P_W2, q, D, 1.0, 0.0, nset, s));
-    TRY(block_dot_batched<T>(cW2, q, q, cW2, q, q, D, P_G, P_part, part_bytes, nset, s));
+    TRY(rowgemm_batched<T>(cW, q, q, P_R1i, q, q, P_W2, q, P_D, D, 1.0, 0.0, nset, s));
+    TRY(block_dot_batched<T>(cW2, q, q, cW2, q, q, P_D, D, P_G, P_part, part_bytes, nset, s));
     chol_batched_kernel<T><<<nset, 64, 0, s>>>(dsp, q, 2, 1e-3, 0.0); note_launch();
-    TRY(rowgemm_batched<T>(cW2, q, q, P_R2i, q, q, P_Vk, q, D, 1.0, 0.0, nset, s));
+    TRY(rowgemm_batched<T>(cW2, q, q, P_R2i, q, q, P_Vk, q, P_D, D, 1.0, 0.0, nset, s));
     beta_batched_kernel<T><<<gq, 128, 0, s>>>(dsp, mb, nb, nb - q, q, append ? 1 : 0); note_launch();
     if (append) {
       const dim3 ga{unsigned((D * q + 255) / 256), unsigned(nset), 1u};
-      append_batched_kernel<T><<<ga, 256, 0, s>>>(dsp, D, q, mb, nb); note_launch();
+      append_batched_kernel<T><<<ga, 256, 0, s>>>(dsp, q, mb, nb); note_launch();
     }
     gather_counts_kernel<T><<<(nset + 127) / 128, 128, 0, s>>>(dsp, nset, dcounts); note_launch();
     TRBL_CUDA(cudaGetLastError());
@@ -1506,7 +1525,7 @@ struct BatchDriver {
     for (int i = 0; i < nset; ++i) failed[i] = rc[i] != TRBL_OK;
     for_sets(0, [&](int i) {
       const int r = sets[i]->finish(evals + size_t(i) * nev, resid ? resid + size_t(i) * nev : nullptr,
-                                    evecs ? static_cast<T*>(evecs) + size_t(i) * D * nev : nullptr, nullptr);
+                                    evecs ? static_cast<T*>(evecs) + voff[i] / q * nev : nullptr, nullptr);
       const cudaError_t e = cudaStreamSynchronize(ss[i]);
       if (r == TRBL_OK && e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize (batched finish)");
       return r;

@@ -67,3 +67,32 @@ def test_apply_autotune_keeps_results():
     W1 = h.apply(V)
     torch.cuda.synchronize()
     assert torch.allclose(W0, W1, rtol=1e-6, atol=1e-6 * W0.abs().max().item())
+
+
+@pytest.mark.parametrize("precision,tol,bar", [(trbl.TRBL_PREC_F64, 1e-10, 1e-9), (trbl.TRBL_PREC_MIXED, 1e-6, 1e-6)])
+def test_batch_sectors_of_uneven_dimension(precision, tol, bar):
+    """Sectors of other particle numbers and 2M (each on its own basis, with
+    its own tables, work list and dimension) in one batched solve: every
+    sector's eigenvalues against dense eigh of the oracle's H, and its Ritz
+    vectors against that H (residual)."""
+    sp = synth.make_space(synth.SPACE12_SHELLS)
+    inter = synth.draw_interaction(sp, sp, 301)
+    sectors = [(2, 2, 0), (2, 2, 2), (3, 2, 1), (2, 3, -1), (1, 3, 0)]
+    bases = [trbl.Basis(sp, kA, sp, kB, tm) for kA, kB, tm in sectors]
+    hs = [trbl.Hamiltonian.from_interaction(b, inter) for b in bases]
+    dims = [b.dim for b in bases]
+    assert len(set(dims)) > 2
+    nev, q, mb = 8, 4, 40
+    ev, rs, X, status, st = trbl.solve_batch(hs, nev, q, mb, tol, precision=precision, want_vectors=True)
+    assert st["rc"] == trbl.TRBL_OK, st["message"]
+    assert status == [0] * len(sectors)
+    assert isinstance(X, list) and [x.shape[0] for x in X] == dims
+    for k, (kA, kB, tm) in enumerate(sectors):
+        B = ob.ProductBasis(sp.twom, kA, sp.twom, kB, tm)
+        H = oh.assemble(B, inter)
+        ref = np.linalg.eigvalsh(H.toarray())
+        normH = max(abs(ref[0]), abs(ref[-1]))
+        assert np.abs(ev[k] - ref[:nev]).max() <= bar * normH, (k, np.abs(ev[k] - ref[:nev]).max())
+        x = X[k].double().cpu().numpy()
+        r = np.linalg.norm(H @ x - x * ev[k], axis=0)
+        assert r.max() <= (1e-8 if precision == trbl.TRBL_PREC_F64 else 1e-4) * normH, (k, r.max() / normH)
