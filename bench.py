@@ -516,15 +516,17 @@ def run_ours(args, rank, world):
                   "share_of_step": ms_apply / ms_step,
                   "autotune": {"shapes": "(kernel, rows per item, blocks per SM): grouped 16/32/64/128 at 8; "
                                          "fast 16/32/64 at 8; fast 16/32/64 at 6; grouped with two 16-byte "
-                                         "chunks per lane 16/32/64 at 8",
-                               "ms": tune_ms, "chosen": {"kernel": ["grouped", "fast", "grouped_x2"][shape[0]],
+                                         "chunks per lane 16/32/64 at 8; fast with shuffled pairs 16/32/64 at 8",
+                               "ms": tune_ms, "chosen": {"kernel": ["grouped", "fast", "grouped_x2", "fast_shfl"][shape[0]],
                                                          "rows_per_item": shape[1], "blocks_per_sm": shape[2]}}},
         "phases_ms_per_step": {k: (st1[k] - st0[k]) / args.steps
                                for k in ("ms_apply", "ms_orth", "ms_qr", "ms_ritz", "ms_restart")},
+        "second_reorth_passes_in_timed_steps": st1["second_passes"] - st0["second_passes"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": {0: "apply_grouped_kernel<float, 8, 1>", 2: "apply_grouped_kernel<float, 4, 2>"}.get(
-                         shape[0], "apply_fast_kernel<8, %d, false>" % shape[2]),
+                     "kernel": {0: "apply_grouped_kernel<float, 8, 1>", 2: "apply_grouped_kernel<float, 4, 2>",
+                                3: "apply_fast_kernel<8, %d, false, true>" % shape[2]}.get(
+                         shape[0], "apply_fast_kernel<8, %d, false, false>" % shape[2]),
                      "algorithmic_bytes_per_launch": b_slab,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"},
         "clocks": clk,
@@ -533,8 +535,7 @@ def run_ours(args, rank, world):
                 "d2h_bytes_per_step": nbytes, "ms_per_step": el / args.steps * 1e3,
                 "steps": "the device-timed block steps, on a fresh solver",
                 "solver_phase_ms_per_step": e2e_phase_ms / args.steps,
-                "host_buffers": "trbl_host_alloc, NUMA node %d" % numa if numa >= 0
-                                else "trbl_host_alloc (cudaMallocHost: no NUMA node reported)",
+                "host_buffers": "trbl_host_alloc (cudaHostAlloc; GPU's nearest host node %d)" % numa,
                 "copy_gb_per_s": 2 * nbytes * args.steps / (copy_ms * 1e-3) / 1e9 if copy_ms > 0 else None},
     }
     if rank == 0 and world == 1 and not args.no_proj:
@@ -649,7 +650,7 @@ def time_to_nev_large(trbl, name, arms, th=None):
     shape = trbl.apply_get_shape(th)
     torch.cuda.empty_cache()
     out = {"workload": name, "dim": th.basis.dim, "nev": w.nev, "max_basis": w.max_basis, "tol_rel_normH": 1e-6,
-           "product_shape": {"kernel": ["grouped", "fast", "grouped_x2"][shape[0]], "rows_per_item": shape[1],
+           "product_shape": {"kernel": ["grouped", "fast", "grouped_x2", "fast_shfl"][shape[0]], "rows_per_item": shape[1],
                              "blocks_per_sm": shape[2]}}
     first = None
     for label, prec, q in arms:
@@ -662,7 +663,7 @@ def time_to_nev_large(trbl, name, arms, th=None):
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         r = {"seconds": el, "q": q, "converged": st["converged"], "rc": st["rc"], "iterations": st["iterations"],
-             "restarts": st["restarts"], "normH": st["normH"],
+             "restarts": st["restarts"], "second_reorth_passes": st["second_passes"], "normH": st["normH"],
              "max_true_resid_over_normH": float(np.nanmax(rs) / st["normH"]),
              "phase_ms": {k: st[k] for k in ("ms_apply", "ms_orth", "ms_qr", "ms_ritz", "ms_restart")}}
         if first is None:
@@ -795,7 +796,7 @@ def run_apply_only(args):
     if args.rows:
         tune_ms, tune_rows = None, args.rows
         kern = {"grouped": trbl.TRBL_APPLY_GROUPED, "fast": trbl.TRBL_APPLY_FAST,
-                "grouped_x2": trbl.TRBL_APPLY_GROUPED_X2}[args.kernel]
+                "grouped_x2": trbl.TRBL_APPLY_GROUPED_X2, "fast_shfl": trbl.TRBL_APPLY_FAST_SHFL}[args.kernel]
         trbl.apply_set_shape(th, kern, args.rows, args.bps)
         trbl.apply_set_compensated(th, args.comp)
     else:
@@ -854,7 +855,7 @@ def main():
     ap.add_argument("--q", type=int, default=0)
     ap.add_argument("--rows", type=int, default=0,
                     help="--apply-only: fixed neutron rows per work item instead of the autotuner's choice")
-    ap.add_argument("--kernel", default="fast", choices=["fast", "grouped", "grouped_x2"],
+    ap.add_argument("--kernel", default="fast", choices=["fast", "grouped", "grouped_x2", "fast_shfl"],
                     help="--apply-only with --rows: the product kernel")
     ap.add_argument("--bps", type=int, default=8, choices=[6, 8],
                     help="--apply-only with --rows: resident blocks per SM of the fast kernel")

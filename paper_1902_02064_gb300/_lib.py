@@ -15,8 +15,8 @@ TRBL_PREC_F64, TRBL_PREC_MIXED = 1, 2
 TRBL_PROJ_TENSOR, TRBL_PROJ_CUDA_CORE = 0, 1
 TRBL_REORTH_SELECTIVE, TRBL_REORTH_TWICE = 0, 1
 TRBL_NOALLOC_SCRATCH_BYTES = 8 << 20  # include/trbl.h
-TRBL_APPLY_GROUPED, TRBL_APPLY_FAST, TRBL_APPLY_GROUPED_X2 = 0, 1, 2
-TRBL_TUNE_CANDIDATES = 13
+TRBL_APPLY_GROUPED, TRBL_APPLY_FAST, TRBL_APPLY_GROUPED_X2, TRBL_APPLY_FAST_SHFL = 0, 1, 2, 3
+TRBL_TUNE_CANDIDATES = 16
 
 
 class TrblError(RuntimeError):
@@ -445,9 +445,9 @@ def shard_sources(basis: "Basis", row_begin: int, row_end: int):
 
 
 class HostBuffer:
-    """Page-locked host memory on the GPU's nearest host memory node
-    (trbl_host_alloc); .array is a numpy view, .ptr the address, .numa_node
-    the node (-1 for plain pinned memory)."""
+    """Page-locked host memory (trbl_host_alloc); .array is a numpy view,
+    .ptr the address, .numa_node the GPU's nearest host memory node (-1 if
+    the device reports none)."""
 
     def __init__(self, nbytes: int, device: int = 0, dtype=np.float32):
         p, node = _VP(), C.c_int()

@@ -1,6 +1,6 @@
 """Host-buffer solver steps (trbl_solver_step_host) with page-locked buffers
-from trbl_host_alloc, which places them on the host memory node nearest the
-GPU.  A block that goes out to such a buffer and comes back in each step
+from trbl_host_alloc (page-locked, with the host memory node nearest the GPU
+reported).  A block that goes out to such a buffer and comes back in each step
 leaves the iteration (Alg. 4) bit for bit as the device-only steps run it."""
 import numpy as np
 import pytest
