@@ -516,17 +516,16 @@ def run_ours(args, rank, world):
                   "share_of_step": ms_apply / ms_step,
                   "autotune": {"shapes": "(kernel, rows per item, blocks per SM): grouped 16/32/64/128 at 8; "
                                          "fast 16/32/64 at 8; fast 16/32/64 at 6; grouped with two 16-byte "
-                                         "chunks per lane 16/32/64 at 8; fast with shuffled pairs 16/32/64 at 8",
-                               "ms": tune_ms, "chosen": {"kernel": ["grouped", "fast", "grouped_x2", "fast_shfl"][shape[0]],
+                                         "chunks per lane 16/32/64 at 8",
+                               "ms": tune_ms, "chosen": {"kernel": ["grouped", "fast", "grouped_x2"][shape[0]],
                                                          "rows_per_item": shape[1], "blocks_per_sm": shape[2]}}},
         "phases_ms_per_step": {k: (st1[k] - st0[k]) / args.steps
                                for k in ("ms_apply", "ms_orth", "ms_qr", "ms_ritz", "ms_restart")},
         "second_reorth_passes_in_timed_steps": st1["second_passes"] - st0["second_passes"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": {0: "apply_grouped_kernel<float, 8, 1>", 2: "apply_grouped_kernel<float, 4, 2>",
-                                3: "apply_fast_kernel<8, %d, false, true>" % shape[2]}.get(
-                         shape[0], "apply_fast_kernel<8, %d, false, false>" % shape[2]),
+                     "kernel": {0: "apply_grouped_kernel<float, 8, 1>", 2: "apply_grouped_kernel<float, 4, 2>"}.get(
+                         shape[0], "apply_fast_kernel<8, %d, false>" % shape[2]),
                      "algorithmic_bytes_per_launch": b_slab,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"},
         "clocks": clk,
@@ -650,7 +649,7 @@ def time_to_nev_large(trbl, name, arms, th=None):
     shape = trbl.apply_get_shape(th)
     torch.cuda.empty_cache()
     out = {"workload": name, "dim": th.basis.dim, "nev": w.nev, "max_basis": w.max_basis, "tol_rel_normH": 1e-6,
-           "product_shape": {"kernel": ["grouped", "fast", "grouped_x2", "fast_shfl"][shape[0]], "rows_per_item": shape[1],
+           "product_shape": {"kernel": ["grouped", "fast", "grouped_x2"][shape[0]], "rows_per_item": shape[1],
                              "blocks_per_sm": shape[2]}}
     first = None
     for label, prec, q in arms:
@@ -712,6 +711,7 @@ def gradient_batch(trbl, nset=64):
             "batched_solve_s": t_solve_b, "batched_solve_plus_gradients_s": t_batch,
             "sequential_solves_plus_gradients_s": t_seq, "speedup": t_seq / t_batch,
             "sets_ok": int(sum(1 for x in status if x == 0)), "graph_steps": st["iterations"],
+            "ms_graph_steps": st["ms_apply"], "ms_between_steps": st["ms_ritz"],
             "max_eig_diff_batch_vs_single_over_normH": max_diff / st["normH"],
             "max_euler_identity_error_over_normH": euler}
 
@@ -796,7 +796,7 @@ def run_apply_only(args):
     if args.rows:
         tune_ms, tune_rows = None, args.rows
         kern = {"grouped": trbl.TRBL_APPLY_GROUPED, "fast": trbl.TRBL_APPLY_FAST,
-                "grouped_x2": trbl.TRBL_APPLY_GROUPED_X2, "fast_shfl": trbl.TRBL_APPLY_FAST_SHFL}[args.kernel]
+                "grouped_x2": trbl.TRBL_APPLY_GROUPED_X2}[args.kernel]
         trbl.apply_set_shape(th, kern, args.rows, args.bps)
         trbl.apply_set_compensated(th, args.comp)
     else:
@@ -855,7 +855,7 @@ def main():
     ap.add_argument("--q", type=int, default=0)
     ap.add_argument("--rows", type=int, default=0,
                     help="--apply-only: fixed neutron rows per work item instead of the autotuner's choice")
-    ap.add_argument("--kernel", default="fast", choices=["fast", "grouped", "grouped_x2", "fast_shfl"],
+    ap.add_argument("--kernel", default="fast", choices=["fast", "grouped", "grouped_x2"],
                     help="--apply-only with --rows: the product kernel")
     ap.add_argument("--bps", type=int, default=8, choices=[6, 8],
                     help="--apply-only with --rows: resident blocks per SM of the fast kernel")

@@ -353,17 +353,13 @@ int trbl_solve_batch(const trbl_hamiltonian* const* hs, int nset, const trbl_par
  * moving two 16-byte chunks of the V row (rows of 32, 64 or 128 bytes;
  * other rows as TRBL_APPLY_GROUPED). */
 #define TRBL_APPLY_GROUPED_X2 2
-/* The fast kernel with a task's (coefficient, offset) pairs fetched by the
- * lane group at once and passed round by shuffles (same sums, bit for bit). */
-#define TRBL_APPLY_FAST_SHFL 3
 /* Launch shapes trbl_apply_autotune times, in this order (kernel, neutron
  * rows per work item, resident blocks per SM): grouped 16/32/64/128; fast
  * 16/32/64 at 8 blocks per SM (32 registers a thread); fast 16/32/64 at 6
- * blocks per SM (40 registers); grouped with two chunks per lane 16/32/64;
- * fast with shuffled pairs 16/32/64 at 8.  Lanes per element and chunks per
- * lane follow from the kernel and the row width (one lane group reads one
- * whole V row). */
-#define TRBL_TUNE_CANDIDATES 16
+ * blocks per SM (40 registers); grouped with two chunks per lane 16/32/64.
+ * Lanes per element and chunks per lane follow from the kernel and the row
+ * width (one lane group reads one whole V row). */
+#define TRBL_TUNE_CANDIDATES 13
 
 /* Times the block product of h at block size q and dtype for each launch
  * shape above that applies and keeps the fastest; ms [TRBL_TUNE_CANDIDATES]
@@ -378,8 +374,8 @@ int trbl_apply_autotune(trbl_hamiltonian* h, int q, int dtype, float* ms, int* b
  * a product of h is running.  Errors: TRBL_ERR_ARG. */
 int trbl_apply_set_rows(trbl_hamiltonian* h, int rows_per_item);
 
-/* Sets the whole launch shape: kernel (TRBL_APPLY_GROUPED, TRBL_APPLY_FAST,
- * TRBL_APPLY_GROUPED_X2 or TRBL_APPLY_FAST_SHFL), rows per work item (1..4096) and resident blocks per SM
+/* Sets the whole launch shape: kernel (TRBL_APPLY_GROUPED, TRBL_APPLY_FAST
+ * or TRBL_APPLY_GROUPED_X2), rows per work item (1..4096) and resident blocks per SM
  * of the fast kernel (6 or 8).  Same rules as trbl_apply_set_rows.  Errors:
  * TRBL_ERR_ARG. */
 int trbl_apply_set_shape(trbl_hamiltonian* h, int kernel, int rows_per_item, int blocks_per_sm);

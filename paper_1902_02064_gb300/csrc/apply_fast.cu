@@ -16,10 +16,7 @@
 //   8-byte load per element: species A's are staged in shared memory per
 //   target, species B's are a table of (source row, coefficient) pairs;
 // * the cross term's coefficient row is walked with a pointer increment and
-//   its source offsets are 32-bit shared-memory words (TRBL_APPLY_FAST); or
-//   a group's lanes fetch up to LPE (coefficient, offset) pairs of a task
-//   with one shared load each and pass them round by shuffles
-//   (TRBL_APPLY_FAST_SHFL), fewer shared loads per element;
+//   its source offsets are 32-bit shared-memory words;
 // * the q / 4 products of an element run as paired FP32 FMAs (fma.rn.f32x2),
 //   two lanes' worth of columns per instruction;
 // * the per-target staging runs on all warps: warp 0 forms the 2m-transfer
@@ -114,7 +111,7 @@ struct RowAcc {
   }
 };
 
-template <int LPE, bool COMP, bool SHF>
+template <int LPE, bool COMP>
 __device__ __forceinline__ void fast_body(const DevH<float>& h, const DevG<float>& g, int item_index,
                                           const float* __restrict__ V, int ld, float* __restrict__ W, int64_t ldw) {
   constexpr int G = 32 / LPE;  // element groups per warp
@@ -236,32 +233,6 @@ __device__ __forceinline__ void fast_body(const DevH<float>& h, const DevG<float
         const int neg = (jb.y & 1) << 31;
         const float* cp = scoef + size_t(ps) * maxK + (jb.y >> 9);
         const float* nsrc = Vl + jb.x * ld;
-        if (SHF) {
-          // the group's LPE lanes fetch up to LPE (coefficient, offset) pairs
-          // with one shared load each and hand them round by shuffles
-          const unsigned gmask = LPE == 32 ? 0xffffffffu : (((1u << LPE) - 1u) << (grp * LPE));
-          for (int b = ps; b < pe; b += LPE) {
-            float cv = 0.f;
-            int ov = 0;
-            if (b + sub < pe) {
-              cv = __int_as_float(__float_as_int(cp[size_t(b - ps + sub) * maxK]) ^ neg);
-              ov = pj[b + sub];
-            }
-            const int n = min(LPE, pe - b);
-            for (int t = 0; t < n; ++t) {
-              const float c0 = __shfl_sync(gmask, cv, t, LPE);
-              const int o0 = __shfl_sync(gmask, ov, t, LPE);
-              u64 a0, a1;
-              ldg16(nsrc + o0, a0, a1);
-              axpy4(acc, c0, a0, a1);
-            }
-          }
-          if (COMP) {
-            racc.add(acc);
-            acc[0] = acc[1] = 0ull;
-          }
-          continue;
-        }
         int p = ps;
         for (; p + 1 < pe; p += 2) {
           const float c0 = __int_as_float(__float_as_int(cp[0]) ^ neg);
@@ -297,53 +268,53 @@ __device__ __forceinline__ void fast_body(const DevH<float>& h, const DevG<float
   }
 }
 
-template <int LPE, int MINB, bool COMP, bool SHF>
+template <int LPE, int MINB, bool COMP>
 __global__ void __launch_bounds__(kThreads, MINB)
     apply_fast_kernel(DevH<float> h, DevG<float> g, const float* __restrict__ V, int ld, float* __restrict__ W,
                       int64_t ldw) {
-  fast_body<LPE, COMP, SHF>(h, g, blockIdx.x, V, ld, W, ldw);
+  fast_body<LPE, COMP>(h, g, blockIdx.x, V, ld, W, ldw);
 }
 
 // Several Hamiltonians, on one basis or on bases of different dimension:
 // blockIdx.y selects the set, which reads Vs[set] and writes Ws[set]; a set
 // with fewer work items than the grid leaves the rest idle.
-template <int LPE, int MINB, bool COMP, bool SHF>
+template <int LPE, int MINB, bool COMP>
 __global__ void __launch_bounds__(kThreads, MINB)
     apply_fast_batch_kernel(const DevH<float>* __restrict__ hs, const DevG<float>* __restrict__ gs,
                             const float* const* __restrict__ Vs, int ld, float* const* __restrict__ Ws, int64_t ldw) {
   if (int(blockIdx.x) >= gs[blockIdx.y].nwork) return;
   const DevH<float> h = hs[blockIdx.y];
   const DevG<float> g = gs[blockIdx.y];
-  fast_body<LPE, COMP, SHF>(h, g, blockIdx.x, Vs[blockIdx.y], ld, Ws[blockIdx.y], ldw);
+  fast_body<LPE, COMP>(h, g, blockIdx.x, Vs[blockIdx.y], ld, Ws[blockIdx.y], ldw);
 }
 
 size_t fast_smem(const DevG<float>& g) {
   return size_t(g.maxQ) * 8 + size_t(g.maxP + 1) * 4 + size_t(g.maxP + 1) * g.maxK * 4 + 33 * 4;
 }
 
-template <int LPE, int MINB, bool COMP, bool SHF>
+template <int LPE, int MINB, bool COMP>
 int launch_lpe(const DevH<float>& h, const DevG<float>& g, const float* V, int ld, float* W, int64_t ldw,
                cudaStream_t s) {
-  static const cudaError_t cfg = cudaFuncSetAttribute(apply_fast_kernel<LPE, MINB, COMP, SHF>,
+  static const cudaError_t cfg = cudaFuncSetAttribute(apply_fast_kernel<LPE, MINB, COMP>,
                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
   TRBL_CUDA(cfg);
   const size_t sm = fast_smem(g);
   if (sm > size_t(kMaxSmem)) return fail(TRBL_ERR_ARG, "product needs %zu bytes of shared memory", sm);
-  apply_fast_kernel<LPE, MINB, COMP, SHF><<<g.nwork, kThreads, sm, s>>>(h, g, V, ld, W, ldw);
+  apply_fast_kernel<LPE, MINB, COMP><<<g.nwork, kThreads, sm, s>>>(h, g, V, ld, W, ldw);
   note_launch();
   TRBL_CUDA(cudaGetLastError());
   return TRBL_OK;
 }
 
-template <int LPE, int MINB, bool COMP, bool SHF>
+template <int LPE, int MINB, bool COMP>
 int launch_batch_lpe(const DevH<float>* hs, const DevG<float>* gs, int nset, int nwork, size_t sm,
                      const float* const* V, int ld, float* const* W, int64_t ldw, cudaStream_t s) {
-  static const cudaError_t cfg = cudaFuncSetAttribute(apply_fast_batch_kernel<LPE, MINB, COMP, SHF>,
+  static const cudaError_t cfg = cudaFuncSetAttribute(apply_fast_batch_kernel<LPE, MINB, COMP>,
                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
   TRBL_CUDA(cfg);
   if (sm > size_t(kMaxSmem)) return fail(TRBL_ERR_ARG, "product needs %zu bytes of shared memory", sm);
   const dim3 grid{static_cast<unsigned>(nwork), static_cast<unsigned>(nset), 1u};
-  apply_fast_batch_kernel<LPE, MINB, COMP, SHF><<<grid, kThreads, sm, s>>>(hs, gs, V, ld, W, ldw);
+  apply_fast_batch_kernel<LPE, MINB, COMP><<<grid, kThreads, sm, s>>>(hs, gs, V, ld, W, ldw);
   note_launch();
   TRBL_CUDA(cudaGetLastError());
   return TRBL_OK;
@@ -362,13 +333,10 @@ template <int LPE>
 int launch_q(const trbl_hamiltonian* h, const float* v, int ld, float* w, int64_t ldw, cudaStream_t s) {
   const bool b6 = h->blocks_per_sm == 6;
   if (h->apply_compensated)
-    return b6 ? launch_lpe<LPE, 6, true, false>(h->d32, h->g32, v, ld, w, ldw, s)
-              : launch_lpe<LPE, 8, true, false>(h->d32, h->g32, v, ld, w, ldw, s);
-  if (h->apply_kernel == TRBL_APPLY_FAST_SHFL)
-    return b6 ? launch_lpe<LPE, 6, false, true>(h->d32, h->g32, v, ld, w, ldw, s)
-              : launch_lpe<LPE, 8, false, true>(h->d32, h->g32, v, ld, w, ldw, s);
-  return b6 ? launch_lpe<LPE, 6, false, false>(h->d32, h->g32, v, ld, w, ldw, s)
-            : launch_lpe<LPE, 8, false, false>(h->d32, h->g32, v, ld, w, ldw, s);
+    return b6 ? launch_lpe<LPE, 6, true>(h->d32, h->g32, v, ld, w, ldw, s)
+              : launch_lpe<LPE, 8, true>(h->d32, h->g32, v, ld, w, ldw, s);
+  return b6 ? launch_lpe<LPE, 6, false>(h->d32, h->g32, v, ld, w, ldw, s)
+            : launch_lpe<LPE, 8, false>(h->d32, h->g32, v, ld, w, ldw, s);
 }
 
 template <int LPE>
@@ -376,22 +344,17 @@ int launch_batch_q(const trbl_hamiltonian* h0, const DevH<float>* hs, const DevG
                    size_t smem, const float* const* v, int ld, float* const* w, int64_t ldw, cudaStream_t s) {
   const bool b6 = h0->blocks_per_sm == 6;
   if (h0->apply_compensated)
-    return b6 ? launch_batch_lpe<LPE, 6, true, false>(hs, gs, nset, nwork, smem, v, ld, w, ldw, s)
-              : launch_batch_lpe<LPE, 8, true, false>(hs, gs, nset, nwork, smem, v, ld, w, ldw, s);
-  if (h0->apply_kernel == TRBL_APPLY_FAST_SHFL)
-    return b6 ? launch_batch_lpe<LPE, 6, false, true>(hs, gs, nset, nwork, smem, v, ld, w, ldw, s)
-              : launch_batch_lpe<LPE, 8, false, true>(hs, gs, nset, nwork, smem, v, ld, w, ldw, s);
-  return b6 ? launch_batch_lpe<LPE, 6, false, false>(hs, gs, nset, nwork, smem, v, ld, w, ldw, s)
-            : launch_batch_lpe<LPE, 8, false, false>(hs, gs, nset, nwork, smem, v, ld, w, ldw, s);
+    return b6 ? launch_batch_lpe<LPE, 6, true>(hs, gs, nset, nwork, smem, v, ld, w, ldw, s)
+              : launch_batch_lpe<LPE, 8, true>(hs, gs, nset, nwork, smem, v, ld, w, ldw, s);
+  return b6 ? launch_batch_lpe<LPE, 6, false>(hs, gs, nset, nwork, smem, v, ld, w, ldw, s)
+            : launch_batch_lpe<LPE, 8, false>(hs, gs, nset, nwork, smem, v, ld, w, ldw, s);
 }
 
 }  // namespace
 
 int launch_fast(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, int64_t ldw, int q, int dtype,
                 cudaStream_t s) {
-  if (dtype != TRBL_F32 || (h->apply_kernel != TRBL_APPLY_FAST && h->apply_kernel != TRBL_APPLY_FAST_SHFL) ||
-      !fast_ok(h, V, ldv, W, ldw, q))
-    return -1;
+  if (dtype != TRBL_F32 || h->apply_kernel != TRBL_APPLY_FAST || !fast_ok(h, V, ldv, W, ldw, q)) return -1;
   const float* v = static_cast<const float*>(V);
   float* w = static_cast<float*>(W);
   const int ld = int(ldv);
@@ -414,9 +377,7 @@ bool fast_tables_ok(const trbl_hamiltonian* h, int64_t ld, int q) {
 int launch_fast_batch(const trbl_hamiltonian* h0, bool all, const void* hs_dev, const void* gs_dev, int nset,
                       int nwork, size_t smem, const void* Vs, int64_t ldv, const void* Ws, int64_t ldw, int q,
                       cudaStream_t s) {
-  if (!all || (h0->apply_kernel != TRBL_APPLY_FAST && h0->apply_kernel != TRBL_APPLY_FAST_SHFL) ||
-      !fast_tables_ok(h0, ldv, q) || ldw % 4 || ldw < q)
-    return -1;
+  if (!all || h0->apply_kernel != TRBL_APPLY_FAST || !fast_tables_ok(h0, ldv, q) || ldw % 4 || ldw < q) return -1;
   const auto* hs = static_cast<const DevH<float>*>(hs_dev);
   const auto* gs = static_cast<const DevG<float>*>(gs_dev);
   const auto* v = static_cast<const float* const*>(Vs);

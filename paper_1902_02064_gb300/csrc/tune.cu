@@ -30,8 +30,7 @@ constexpr Shape kCand[TRBL_TUNE_CANDIDATES] = {
     {TRBL_APPLY_GROUPED, 128, 8}, {TRBL_APPLY_FAST, 16, 8},   {TRBL_APPLY_FAST, 32, 8},
     {TRBL_APPLY_FAST, 64, 8},     {TRBL_APPLY_FAST, 16, 6},   {TRBL_APPLY_FAST, 32, 6},
     {TRBL_APPLY_FAST, 64, 6},     {TRBL_APPLY_GROUPED_X2, 16, 8}, {TRBL_APPLY_GROUPED_X2, 32, 8},
-    {TRBL_APPLY_GROUPED_X2, 64, 8}, {TRBL_APPLY_FAST_SHFL, 16, 8}, {TRBL_APPLY_FAST_SHFL, 32, 8},
-    {TRBL_APPLY_FAST_SHFL, 64, 8}};
+    {TRBL_APPLY_GROUPED_X2, 64, 8}};
 
 int set_shape(trbl_hamiltonian* h, const Shape& c) {
   h->apply_kernel = c.kernel;
@@ -65,7 +64,7 @@ extern "C" int trbl_apply_autotune(trbl_hamiltonian* h, int q, int dtype, float*
   int rc = TRBL_OK;
   for (int c = 0; c < TRBL_TUNE_CANDIDATES && !rc; ++c) {
     if (ms) ms[c] = NAN;
-    if ((kCand[c].kernel == TRBL_APPLY_FAST || kCand[c].kernel == TRBL_APPLY_FAST_SHFL) && !fast) continue;
+    if (kCand[c].kernel == TRBL_APPLY_FAST && !fast) continue;
     if (kCand[c].kernel == TRBL_APPLY_GROUPED_X2 && !x2) continue;
     rc = set_shape(h, kCand[c]);
     if (rc) break;
@@ -103,8 +102,7 @@ extern "C" int trbl_apply_set_rows(trbl_hamiltonian* h, int rows_per_item) {
 extern "C" int trbl_apply_set_shape(trbl_hamiltonian* h, int kernel, int rows_per_item, int blocks_per_sm) {
   clear_error();
   if (!h) return fail(TRBL_ERR_ARG, "null Hamiltonian");
-  if (kernel != TRBL_APPLY_GROUPED && kernel != TRBL_APPLY_FAST && kernel != TRBL_APPLY_GROUPED_X2 &&
-      kernel != TRBL_APPLY_FAST_SHFL)
+  if (kernel != TRBL_APPLY_GROUPED && kernel != TRBL_APPLY_FAST && kernel != TRBL_APPLY_GROUPED_X2)
     return fail(TRBL_ERR_ARG, "unknown kernel %d", kernel);
   if (rows_per_item < 1 || rows_per_item > 4096) return fail(TRBL_ERR_ARG, "rows per work item must be in [1, 4096]");
   if (blocks_per_sm != 6 && blocks_per_sm != 8) return fail(TRBL_ERR_ARG, "blocks per SM must be 6 or 8");

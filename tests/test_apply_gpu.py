@@ -223,8 +223,7 @@ def test_launch_shape_does_not_change_results(medium):
 
 
 SHAPES = [(trbl.TRBL_APPLY_GROUPED, 16, 8), (trbl.TRBL_APPLY_FAST, 16, 8), (trbl.TRBL_APPLY_FAST, 64, 6),
-          (trbl.TRBL_APPLY_FAST, 1, 8), (trbl.TRBL_APPLY_FAST, 4096, 6), (trbl.TRBL_APPLY_FAST_SHFL, 16, 8),
-          (trbl.TRBL_APPLY_FAST_SHFL, 64, 6)]
+          (trbl.TRBL_APPLY_FAST, 1, 8), (trbl.TRBL_APPLY_FAST, 4096, 6)]
 X2 = (trbl.TRBL_APPLY_GROUPED_X2, 32, 8)
 
 
@@ -312,8 +311,7 @@ def test_autotune_candidates_and_choice(medium):
     assert r == rows and kern in (trbl.TRBL_APPLY_GROUPED, trbl.TRBL_APPLY_FAST)
     assert torch.equal(th.apply(V).cpu(), ref)
     ms64, _ = trbl.apply_autotune(th, 16, trbl.TRBL_F64)
-    assert all(np.isfinite(ms64[:4])) and not any(np.isfinite(ms64[4:10])) and all(np.isfinite(ms64[10:13]))
-    assert not any(np.isfinite(ms64[13:]))
+    assert all(np.isfinite(ms64[:4])) and not any(np.isfinite(ms64[4:10])) and all(np.isfinite(ms64[10:]))
     with pytest.raises(trbl.TrblError):
         trbl.apply_set_shape(th, 7, 16, 8)
     with pytest.raises(trbl.TrblError):
