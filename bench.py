@@ -5,7 +5,9 @@ Rayleigh-Ritz), basis of up to 1024 vectors.
 
 One step = one block iteration of the solver: W = H V_k (matrix elements
 generated on the fly), full reorthogonalisation against the stored basis
-(classical Gram-Schmidt twice), Cholesky QR twice, Rayleigh-Ritz on the
+(selective: a pass against the last two blocks, one full classical
+Gram-Schmidt pass, a second one when the DGKS norm test asks for it),
+Cholesky QR twice, Rayleigh-Ritz on the
 projected matrix, and a thick restart when the basis is full.  The
 Hamiltonian's tables are built once before timing.
 
@@ -504,6 +506,7 @@ def run_ours(args, rank, world):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "dim": D, "q": q, "nev": w.nev, "max_basis": w.max_basis,
                    "precision": "mixed (FP32 vectors/apply, FP64 coefficients, CholQR2, Ritz)",
+                   "reorthogonalisation": "selective (local pass, one full pass, second pass on the DGKS test)",
                    "structural_nnz": nnz,
                    "steps": "steady state: the solver is taken through its first thick restart before the "
                             "warm-up; Rayleigh-Ritz at the solver's adaptive cadence",

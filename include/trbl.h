@@ -146,10 +146,14 @@ int trbl_apply_block(const trbl_hamiltonian* h, const void* V, int64_t ldv, void
  * ldw >= q; C is a device FP64 array, row-major m x q (leading dimension
  * q), overwritten.  Products are summed in dtype inside fixed row chunks and
  * the chunk sums are added in FP64 in a fixed order (bit-reproducible for
- * given sizes).  1 <= q <= 64, m >= 1.  The partial-sum scratch
- * (chunks x m x q doubles) is taken with cudaMallocAsync and released with
- * cudaFreeAsync on the stream.  Asynchronous on stream.  Errors:
- * TRBL_ERR_ARG, TRBL_ERR_OOM, TRBL_ERR_CUDA. */
+ * given sizes).  1 <= q <= 64, m >= 1.  A Gram matrix of FP32 data (B ==
+ * W, ldb == ldw, m == q with q = 8, 16, 32 or 64: the "W^T W" of the block
+ * Cholesky QR) goes to a kernel that reads the block once, with products
+ * summed in FP32 over runs of at most 32 rows and the runs in FP64.  The
+ * partial-sum scratch (chunks x m x q doubles) is taken with
+ * cudaMallocAsync and released with cudaFreeAsync on the stream.
+ * Asynchronous on stream.  Errors: TRBL_ERR_ARG, TRBL_ERR_OOM,
+ * TRBL_ERR_CUDA. */
 int trbl_block_dot(const void* B, int64_t ldb, int m, const void* W, int64_t ldw, int q, int64_t D,
                    int dtype, double* C, void* stream);
 

@@ -814,6 +814,262 @@ int rowgemm_ws(const T* In, int64_t ldi, int K, const double* U, int64_t ldu, in
   return rowgemm<T>(In, ldi, K, U, ldu, n, Out, ldo, D, alpha, beta, s);
 }
 
+// Squared column norms of a D x q block (row-major, ld ldw): one block per
+// row range, thread t on column t mod q; FP32 data is squared and summed in
+// FP32 over runs of 32 rows, the runs in FP64; the block's columns are
+// reduced in a fixed order into partial[block][c].
+template <typename T>
+__global__ void col_sumsq_kernel(const T* __restrict__ W, int64_t ldw, int q, int64_t D, int64_t rows_per_block,
+                                 double* __restrict__ partial) {
+  __shared__ double red[256];
+  const int t = threadIdx.x;
+  const int per = blockDim.x / q;  // rows per sweep
+  const int c = t % q, rl = t / q;
+  double acc = 0.0;
+  if (rl < per) {
+    const int64_t r0 = int64_t(blockIdx.x) * rows_per_block;
+    const int64_t r1 = r0 + rows_per_block < D ? r0 + rows_per_block : D;
+    if constexpr (std::is_same<T, float>::value) {
+      float run = 0.f;
+      int cnt = 0;
+      for (int64_t r = r0 + rl; r < r1; r += per) {
+        const float x = W[r * ldw + c];
+        run = fmaf(x, x, run);
+        if (++cnt == 32) {
+          acc += double(run);
+          run = 0.f;
+          cnt = 0;
+        }
+      }
+      acc += double(run);
+    } else {
+      for (int64_t r = r0 + rl; r < r1; r += per) {
+        const double x = W[r * ldw + c];
+        acc = fma(x, x, acc);
+      }
+    }
+  }
+  red[t] = acc;
+  __syncthreads();
+  if (t < q) {
+    double v = 0.0;
+    for (int k = 0; k < per; ++k) v += red[k * q + t];
+    partial[int64_t(blockIdx.x) * q + t] = v;
+  }
+}
+
+// The same for a contiguous FP32 block (ldw = q, q a multiple of 4 dividing
+// 128, 16-byte aligned) read as float4s: float4 i of the block covers
+// columns 4 i mod q .. + 3, so thread t of a block whose range starts on a
+// row boundary keeps columns 4 t mod q .. + 3 while striding by 256
+// float4s.  Four loads in flight per thread; FP32 runs of 32 float4s, FP64
+// beyond; threads with the same columns are summed in a fixed order.
+__global__ void __launch_bounds__(256) col_sumsq_vec_kernel(const float* __restrict__ W, int q, int64_t D,
+                                                            int64_t rows_per_block, double* __restrict__ partial) {
+  __shared__ double red[256][4];
+  const int t = threadIdx.x;
+  const int64_t r0 = int64_t(blockIdx.x) * rows_per_block;
+  const int64_t r1 = r0 + rows_per_block < D ? r0 + rows_per_block : D;
+  const float4* p = reinterpret_cast<const float4*>(W) + r0 * (q / 4);
+  const int64_t n4 = r1 > r0 ? (r1 - r0) * (q / 4) : 0;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  float run[4] = {0.f, 0.f, 0.f, 0.f};
+  int cnt = 0;
+  int64_t i = t;
+  for (; i + 3 * 256 < n4; i += 4 * 256) {
+    float4 x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = __ldg(p + i + 256 * u);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      run[0] = fmaf(x[u].x, x[u].x, run[0]);
+      run[1] = fmaf(x[u].y, x[u].y, run[1]);
+      run[2] = fmaf(x[u].z, x[u].z, run[2]);
+      run[3] = fmaf(x[u].w, x[u].w, run[3]);
+    }
+    if (++cnt == 8) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[k] += double(run[k]), run[k] = 0.f;
+      cnt = 0;
+    }
+  }
+  for (; i < n4; i += 256) {
+    const float4 x = __ldg(p + i);
+    run[0] = fmaf(x.x, x.x, run[0]);
+    run[1] = fmaf(x.y, x.y, run[1]);
+    run[2] = fmaf(x.z, x.z, run[2]);
+    run[3] = fmaf(x.w, x.w, run[3]);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) red[t][k] = acc[k] + double(run[k]);
+  __syncthreads();
+  if (t < q) {
+    const int q4 = q / 4;
+    double v = 0.0;
+    for (int j = t / 4; j < 256; j += q4) v += red[j][t % 4];
+    partial[int64_t(blockIdx.x) * q + t] = v;
+  }
+}
+
+// Gram matrix G = W^T W of a D x Q block of FP32 data (Q = 8, 16, 32 or
+// 64), FP64 result.  A block stages 16 KB of rows (4096 / Q) at a time in
+// shared memory, the next chunk's loads in flight (in registers) while the
+// current one is used; (Q/4)^2 threads each own a 4 x 4 tile of G and
+// 256 / (Q/4)^2 row groups split the staged rows; products are summed in
+// FP32 over runs of at most 32 rows of a thread, the runs into a two-word
+// FP32 sum by TwoSum (error-free; GB300's FP64 adds are too slow to take
+// every run) and that sum into FP64 at the end.  The
+// row groups' sums are reduced in a fixed order into partial[block] (the
+// staging buffer's shared memory reused), the blocks' by
+// reduce_partials_kernel: the result does not depend on timing.
+template <int Q>
+__global__ void __launch_bounds__(256, 2) gram_f32_kernel(const float* __restrict__ W, int64_t ldw, int64_t D,
+                                                          int64_t rows_per_block, double* __restrict__ partial) {
+  constexpr int kRows = 4096 / Q;
+  constexpr int TQ = Q / 4;                 // tiles per side
+  constexpr int kGroups = 256 / (TQ * TQ);  // row groups
+  constexpr int kBytes = kRows * Q * 4 > Q * Q * 8 ? kRows * Q * 4 : Q * Q * 8;
+  __shared__ __align__(16) unsigned char sm[kBytes];
+  float* xs = reinterpret_cast<float*>(sm);
+  double* red = reinterpret_cast<double*>(sm);
+  const int t = threadIdx.x;
+  const int tile = t % (TQ * TQ), grp = t / (TQ * TQ);
+  const int ti = tile / TQ, tj = tile % TQ;
+  const int64_t r0 = int64_t(blockIdx.x) * rows_per_block;
+  const int64_t r1 = r0 + rows_per_block < D ? r0 + rows_per_block : D;
+  const bool vec = (ldw % 4) == 0 && (reinterpret_cast<uintptr_t>(W) & 15) == 0;
+  float hi[4][4], lo[4][4], run[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) hi[a][b] = lo[a][b] = run[a][b] = 0.f;
+  // hi + lo += run exactly (Knuth's TwoSum; round-to-nearest adds the
+  // compiler may not contract or reorder), then run = 0
+  auto flush = [&]() {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const float x = run[a][b], h = hi[a][b];
+        const float sum = __fadd_rn(h, x);
+        const float xb = __fsub_rn(sum, h);
+        const float hb = __fsub_rn(sum, xb);
+        lo[a][b] = __fadd_rn(lo[a][b], __fadd_rn(__fsub_rn(h, hb), __fsub_rn(x, xb)));
+        hi[a][b] = sum;
+        run[a][b] = 0.f;
+      }
+  };
+  // chunk loads: float4 e = t + 256 u (u < 4) is row e / (Q/4), columns 4 (e mod Q/4) ..
+  float4 pre[4];
+  auto load = [&](int64_t c0) {
+    const int nr = int(r1 - c0 < kRows ? r1 - c0 : kRows);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = t + 256 * u, rr = e / (Q / 4), cc = e % (Q / 4);
+      pre[u] = rr < nr ? __ldg(reinterpret_cast<const float4*>(W + (c0 + rr) * ldw + 4 * cc))
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  if (vec && r0 < r1) load(r0);
+  int cnt = 0;
+  for (int64_t c0 = r0; c0 < r1; c0 += kRows) {
+    const int nr = int(r1 - c0 < kRows ? r1 - c0 : kRows);
+    __syncthreads();
+    if (vec) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = t + 256 * u;
+        *reinterpret_cast<float4*>(xs + 4 * e) = pre[u];
+      }
+    } else {
+      for (int e = t; e < kRows * Q; e += 256) {
+        const int rr = e / Q, cc = e % Q;
+        xs[e] = rr < nr ? W[(c0 + rr) * ldw + cc] : 0.f;
+      }
+    }
+    __syncthreads();
+    if (vec && c0 + kRows < r1) load(c0 + kRows);
+    for (int rr = grp; rr < nr; rr += kGroups) {
+      const float4 x = *reinterpret_cast<const float4*>(xs + rr * Q + 4 * ti);
+      const float4 y = *reinterpret_cast<const float4*>(xs + rr * Q + 4 * tj);
+      const float xa[4] = {x.x, x.y, x.z, x.w}, ya[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) run[a][b] = fmaf(xa[a], ya[b], run[a][b]);
+      if (++cnt == 32) {
+        flush();
+        cnt = 0;
+      }
+    }
+  }
+  flush();
+  // row groups in order 0, 1, ... into red (the first barrier also ends
+  // every thread's reads of the staged rows)
+  for (int g = 0; g < kGroups; ++g) {
+    __syncthreads();
+    if (grp == g) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const double v = double(hi[a][b]) + double(lo[a][b]);
+          double& d = red[(4 * ti + a) * Q + 4 * tj + b];
+          d = g == 0 ? v : d + v;
+        }
+    }
+  }
+  __syncthreads();
+  for (int e = t; e < Q * Q; e += 256) partial[int64_t(blockIdx.x) * Q * Q + e] = red[e];
+}
+
+template <int Q>
+int gram_f32_launch(const float* W, int64_t ldw, int64_t D, double* G, Workspace& ws, cudaStream_t s) {
+  int64_t nblk = std::min<int64_t>(int64_t(4) * ws.sm_count, (D + 4096 / Q - 1) / (4096 / Q));
+  nblk = std::max<int64_t>(1, std::min<int64_t>(nblk, int64_t(ws.partial_bytes / (sizeof(double) * Q * Q))));
+  const int64_t rows = (D + nblk - 1) / nblk;
+  nblk = (D + rows - 1) / rows;
+  gram_f32_kernel<Q><<<unsigned(nblk), 256, 0, s>>>(W, ldw, D, rows, ws.partial); note_launch();
+  TRBL_CUDA(cudaGetLastError());
+  reduce_partials_kernel<<<(Q * Q + 255) / 256, 256, 0, s>>>(ws.partial, int(nblk), Q * Q, G); note_launch();
+  TRBL_CUDA(cudaGetLastError());
+  return TRBL_OK;
+}
+
+template <typename T>
+int col_sumsq(const T* W, int64_t ldw, int q, int64_t D, double* out, Workspace& ws, cudaStream_t s) {
+  if (q <= 0 || q > 256 || D <= 0) return fail(TRBL_ERR_ARG, "col_sumsq: q=%d D=%lld", q, (long long)D);
+  int64_t nblk = std::min<int64_t>(int64_t(4) * ws.sm_count, (D + 255) / 256);
+  nblk = std::max<int64_t>(1, std::min<int64_t>(nblk, int64_t(ws.partial_bytes / (sizeof(double) * q))));
+  const int64_t rows = (D + nblk - 1) / nblk;
+  nblk = (D + rows - 1) / rows;
+  bool vec = false;
+  if constexpr (std::is_same<T, float>::value)
+    vec = ldw == q && q % 4 == 0 && 128 % q == 0 && (reinterpret_cast<uintptr_t>(W) & 15) == 0;
+  if (vec)
+    col_sumsq_vec_kernel<<<unsigned(nblk), 256, 0, s>>>(reinterpret_cast<const float*>(W), q, D, rows, ws.partial);
+  else
+    col_sumsq_kernel<T><<<unsigned(nblk), 256, 0, s>>>(W, ldw, q, D, rows, ws.partial);
+  note_launch();
+  TRBL_CUDA(cudaGetLastError());
+  reduce_partials_kernel<<<(q + 255) / 256, 256, 0, s>>>(ws.partial, int(nblk), q, out); note_launch();
+  TRBL_CUDA(cudaGetLastError());
+  return TRBL_OK;
+}
+
+template <typename T>
+int gram(const T* W, int64_t ldw, int q, int64_t D, double* G, Workspace& ws, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (D > 0 && ldw >= q) {
+      if (q == 8) return gram_f32_launch<8>(W, ldw, D, G, ws, s);
+      if (q == 16) return gram_f32_launch<16>(W, ldw, D, G, ws, s);
+      if (q == 32) return gram_f32_launch<32>(W, ldw, D, G, ws, s);
+      if (q == 64) return gram_f32_launch<64>(W, ldw, D, G, ws, s);
+    }
+  }
+  return block_dot<T>(W, ldw, q, W, ldw, q, D, G, ws, s);
+}
+
 template <typename S, typename T>
 int copy_cols(const S* src, int64_t lds, T* dst, int64_t ldd, int64_t D, int ncol, cudaStream_t s) {
   if (ncol <= 0 || D <= 0) return TRBL_OK;
@@ -844,6 +1100,10 @@ template int block_dot<double>(const double*, int64_t, int, const double*, int64
 template int rowgemm<float>(const float*, int64_t, int, const double*, int64_t, int, float*, int64_t, int64_t, double, double, cudaStream_t);
 template int rowgemm<double>(const double*, int64_t, int, const double*, int64_t, int, double*, int64_t, int64_t, double, double, cudaStream_t);
 template int rowgemm_ws<float>(const float*, int64_t, int, const double*, int64_t, int, float*, int64_t, int64_t, double, double, Workspace&, cudaStream_t);
+template int col_sumsq<float>(const float*, int64_t, int, int64_t, double*, Workspace&, cudaStream_t);
+template int gram<float>(const float*, int64_t, int, int64_t, double*, Workspace&, cudaStream_t);
+template int gram<double>(const double*, int64_t, int, int64_t, double*, Workspace&, cudaStream_t);
+template int col_sumsq<double>(const double*, int64_t, int, int64_t, double*, Workspace&, cudaStream_t);
 template int rowgemm_ws<double>(const double*, int64_t, int, const double*, int64_t, int, double*, int64_t, int64_t, double, double, Workspace&, cudaStream_t);
 template int copy_cols<float, float>(const float*, int64_t, float*, int64_t, int64_t, int, cudaStream_t);
 template int copy_cols<double, double>(const double*, int64_t, double*, int64_t, int64_t, int, cudaStream_t);

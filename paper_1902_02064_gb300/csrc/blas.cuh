@@ -58,6 +58,15 @@ template <typename T>
 int rowgemm_ws(const T* In, int64_t ldi, int K, const double* U, int64_t ldu, int n, T* Out, int64_t ldo, int64_t D,
                double alpha, double beta, Workspace& ws, cudaStream_t s);
 
+// G = W^T W (q x q, FP64) for a D x q block: a CUDA-core Gram kernel for
+// FP32 data with q = 8, 16, 32 or 64, block_dot otherwise; deterministic.
+template <typename T>
+int gram(const T* W, int64_t ldw, int q, int64_t D, double* G, Workspace& ws, cudaStream_t s);
+
+// out[c] = sum_r W[r][c]^2 for a D x q block (q <= 256), deterministic.
+template <typename T>
+int col_sumsq(const T* W, int64_t ldw, int q, int64_t D, double* out, Workspace& ws, cudaStream_t s);
+
 // Tensor-core (tcgen05, split TF32) forms for FP32 data, n / q <= 32
 // (proj_tc.cu); -1 when the shapes, alignment or workspace do not allow them.
 int block_dot_tc(const float* B, int64_t ldb, int m, const float* W, int64_t ldw, int q, int64_t D, double* C,

@@ -27,7 +27,7 @@
 //   (128-byte swizzle) into a ring of four raw stages;
 // * warps 2-9 (256 threads) convert a raw stage into split K-major operand
 //   tiles (a transpose for the projection, whose operands are row-major in
-//   K) in one of three conversion buffers, then release the raw stage, and
+//   K) in one of two conversion buffers, then release the raw stage, and
 //   read a finished accumulator out one stage later, when its MMAs have
 //   had a stage's time to complete;
 // * warp 1 (one lane) issues the stage's MMAs and commits them to an
@@ -61,7 +61,7 @@ constexpr int kRawStages = 4;
 constexpr int kDrain = 4;           // projection stages per accumulator segment
 constexpr int kTile = 128;          // MMA M: columns of B (projection) or rows of In (update)
 constexpr int kN = 32;              // MMA N (one accumulator = 32 tensor-memory columns)
-constexpr int kConvBufs = 3;
+constexpr int kConvBufs = 2;
 constexpr uint32_t kTmemCols = 128;  // two accumulators of 64 columns (hi*hi + lo*hi | hi*lo)
 constexpr uint32_t kIdesc = idesc_tf32(kTile, kN);
 constexpr uint32_t kIdesc2 = idesc_tf32(kTile, 2 * kN);

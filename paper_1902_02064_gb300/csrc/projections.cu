@@ -41,7 +41,14 @@ extern "C" int trbl_block_dot(const void* B, int64_t ldb, int m, const void* W, 
   const size_t bytes = block_dot_workspace_bytes(m, q, sms);
   void* part = nullptr;
   TRBL_CUDA(cudaMallocAsync(&part, bytes, s));
-  if (dtype == TRBL_F64)
+  if (dtype == TRBL_F32 && B == W && ldb == ldw && m == q && (q == 8 || q == 16 || q == 32 || q == 64)) {
+    // a Gram matrix: the dedicated kernel reads the block once
+    Workspace ws;
+    ws.partial = static_cast<double*>(part);
+    ws.partial_bytes = bytes;
+    ws.sm_count = sms;
+    rc = gram<float>(static_cast<const float*>(W), ldw, q, D, C, ws, s);
+  } else if (dtype == TRBL_F64)
     rc = block_dot_capped<double>(static_cast<const double*>(B), ldb, m, static_cast<const double*>(W), ldw, q, D, C,
                                   static_cast<double*>(part), bytes, sms, s);
   else

@@ -442,7 +442,8 @@ struct Solver {
   T *basis, *Vk, *W, *W2, *Wsave, *panel;
   int64_t panel_rows;
   double *C, *G, *R1, *R1i, *R2, *R2i, *beta, *Tm, *Aw, *theta, *Ut, *res, *syev_work, *Xd, *HXd, *rpart, *rtrue;
-  double *Cl, *Gn;  // local-pass coefficients (2q x q), block Gram matrices before / after the full pass
+  double *Cl, *Gn;  // local-pass coefficients (up to (2q + 3) x q), squared column norms before the full pass
+  bool gram_ready = false;  // G holds W^T W of the current W (set by the selective pass)
   int second_passes = 0;
   int *flags, *devinfo;
   int lwork;
@@ -485,21 +486,32 @@ struct Solver {
   // in the first (Daniel-Gragg-Kaufman-Stewart).  C1's rows nb-q .. nb
   // receive the projection of W onto V_k summed over the passes.
   int cgs_selective(T* Wb, int nb, double* C1) {
-    const int ql = std::min(2 * q, nb);
-    const T* Bl = basis + (nb - ql);
+    // The local window ends at column nb and starts on a 16-byte boundary
+    // (after a thick restart nb = l_s + q is odd in general; a window at an
+    // unaligned column would leave the TMA and tensor-core kernels for the
+    // generic ones), so it may hold up to 3 columns more than 2q.
+    constexpr int kAlign = int(16 / sizeof(T));
+    const int c0 = std::max(0, nb - 2 * q) / kAlign * kAlign;
+    const int ql = nb - c0;
+    const T* Bl = basis + c0;
     TRY(block_dot<T>(Bl, mb, ql, Wb, q, q, D, Cl, ws, s));
     TRY(rowgemm_ws<T>(Bl, mb, ql, Cl, q, q, Wb, q, D, -1.0, 1.0, ws, s));
-    TRY(block_dot<T>(Wb, q, q, Wb, q, q, D, Gn, ws, s));
+    // squared column norms before the full pass, and after it the block's
+    // Gram matrix, whose diagonal holds them after (the DGKS test) and which
+    // the block QR reuses when no second pass follows
+    TRY(col_sumsq<T>(Wb, q, q, D, Gn, ws, s));
     TRY(block_dot<T>(basis, mb, nb, Wb, q, q, D, C, ws, s));
     TRY(rowgemm_ws<T>(basis, mb, nb, C, q, q, Wb, q, D, -1.0, 1.0, ws, s));
-    TRY(block_dot<T>(Wb, q, q, Wb, q, q, D, Gn + q * q, ws, s));
-    TRBL_CUDA(cudaMemcpyAsync(hbuf + 2 * mb, Gn, sizeof(double) * 2 * q * q, cudaMemcpyDeviceToHost, s));
+    TRY(gram<T>(Wb, q, q, D, G, ws, s));
+    TRBL_CUDA(cudaMemcpyAsync(hbuf + 2 * mb, Gn, sizeof(double) * q, cudaMemcpyDeviceToHost, s));
+    TRBL_CUDA(cudaMemcpyAsync(hbuf + 2 * mb + q, G, sizeof(double) * q * q, cudaMemcpyDeviceToHost, s));
     TRBL_CUDA(cudaStreamSynchronize(s));
     bool again = false;
     for (int j = 0; j < q; ++j) {
-      const double before = hbuf[2 * mb + j * q + j], after = hbuf[2 * mb + q * q + j * q + j];
+      const double before = hbuf[2 * mb + j], after = hbuf[2 * mb + q + j * q + j];
       if (!(after > 0.5 * before)) again = true;  // also catches NaN and a vanished column
     }
+    gram_ready = !again && Wb == W;
     double* C2 = nullptr;
     if (again) {
       C2 = C + size_t(mb) * q;
@@ -525,12 +537,13 @@ struct Solver {
   // Cholesky QR twice, enqueued only: the deficiency counts are copied to
   // pinned host memory (hflags) for the caller to read after synchronising.
   int cholqr2_async(T* Win, double thresh_abs, double thresh_rel, double thresh_max) {
-    TRY(block_dot<T>(Win, q, q, Win, q, q, D, G, ws, s));
+    if (!(gram_ready && Win == W)) TRY(gram<T>(Win, q, q, D, G, ws, s));
+    gram_ready = false;
     chol_kernel<<<1, 64, 0, s>>>(G, q, thresh_abs, thresh_rel, thresh_max, R1, R1i, flags + kF1); note_launch();
     TRBL_CUDA(cudaGetLastError());
     TRBL_CUDA(cudaMemcpyAsync(hflags + kF1, flags + kF1, sizeof(int) * (q + 1), cudaMemcpyDeviceToHost, s));
     TRY(rowgemm_ws<T>(Win, q, q, R1i, q, q, W2, q, D, 1.0, 0.0, ws, s));
-    TRY(block_dot<T>(W2, q, q, W2, q, q, D, G, ws, s));
+    TRY(gram<T>(W2, q, q, D, G, ws, s));
     chol_kernel<<<1, 64, 0, s>>>(G, q, 0.0, 1e-3, 0.0, R2, R2i, flags + kF2); note_launch();
     TRBL_CUDA(cudaGetLastError());
     TRBL_CUDA(cudaMemcpyAsync(hflags + kF2, flags + kF2, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1042,8 +1055,8 @@ struct Solver {
       Wsave = ar.take<T>(dq);
       panel = ar.take<T>(size_t(panel_rows) * ((ls + 7) / 8 * 8));
       C = ar.take<double>(size_t(3) * mb * q);
-      Cl = ar.take<double>(size_t(2) * q * q);
-      Gn = ar.take<double>(size_t(2) * q * q);
+      Cl = ar.take<double>(size_t(2 * q + 4) * q);
+      Gn = ar.take<double>(q);
       G = ar.take<double>(q * q);
       R1 = ar.take<double>(q * q);
       R1i = ar.take<double>(q * q);

@@ -63,3 +63,23 @@ def test_narrow_fp64_dot_and_update(D, m, q):
     ref = -(Bh @ U) + 0.5 * O0
     bound = np.abs(Bh) @ np.abs(U) + 0.5 * np.abs(O0)
     assert np.all(np.abs(Out.cpu().numpy() - ref) <= 1e-12 * bound + 1e-300)
+
+
+@pytest.mark.parametrize("q", [8, 16, 32, 64])
+@pytest.mark.parametrize("D,ld", [(1, 0), (127, 0), (100003, 0), (33333, 5), (300000, 1)])
+def test_gram_kernel_matches_numpy(q, D, ld):
+    """The Gram matrix W^T W of FP32 data (the block Cholesky QR's input)
+    through the dedicated kernel: contiguous blocks, blocks inside a wider
+    array (leading dimension q + ld, unaligned rows when q + ld is not a
+    multiple of 4), ragged row counts; symmetric to the last bit because
+    (i, j) and (j, i) see the same products in the same order."""
+    full = torch.from_numpy(synth.random_block(D, q + ld, 40 + q)).float().cuda()
+    W = full[:, :q]
+    G = trbl.block_dot(W, W).cpu().numpy()
+    Wd = W.double().cpu().numpy()
+    ref = Wd.T @ Wd
+    bound = np.abs(Wd).T @ np.abs(Wd)
+    assert np.all(np.abs(G - ref) <= 4e-6 * bound + 1e-300)
+    assert np.array_equal(G, G.T)
+    G2 = trbl.block_dot(W, W).cpu().numpy()
+    assert np.array_equal(G, G2)
