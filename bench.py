@@ -450,11 +450,15 @@ def run_ours(args, rank, world):
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     barrier()
+    # the timed steps are the profiler's range (ncu --profile-from-start off
+    # captures exactly them; without a profiler these calls do nothing)
+    torch.cuda.profiler.start()
     e0.record(stream)
     for _ in range(args.steps):
         sv.step()
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     barrier()
     clk = clocks.stop()
     launches = trbl.trbl_kernel_launches() - l0
