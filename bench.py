@@ -719,6 +719,7 @@ def gradient_batch(trbl, nset=64):
             "sequential_solves_plus_gradients_s": t_seq, "speedup": t_seq / t_batch,
             "sets_ok": int(sum(1 for x in status if x == 0)), "graph_steps": st["iterations"],
             "ms_graph_steps": st["ms_apply"], "ms_between_steps": st["ms_ritz"],
+            "second_reorth_set_steps": st["second_passes"],
             "max_eig_diff_batch_vs_single_over_normH": max_diff / st["normH"],
             "max_euler_identity_error_over_normH": euler}
 

@@ -331,7 +331,11 @@ int trbl_solve(const trbl_hamiltonian* h, const trbl_params* p, double* evals, d
  * sets testing at the same steps.  stats: iterations = block steps, ms_total
  * = wall time of the whole call, ms_apply = wall time of the batched block
  * steps (product, orthogonalisation, QR of every set), ms_ritz = wall time
- * of the tests and restarts between them.  The Hamiltonians may live on one
+ * of the tests and restarts between them, second_passes = set-steps that
+ * ran a second full reorthogonalisation pass (the selective schedule takes
+ * its DGKS decision per set on the device, inside the captured step: the
+ * second pass's launches return at once for the sets that skip it).  The
+ * Hamiltonians may live on one
  * basis (parameter sets) or on bases of different dimension (sectors of
  * other 2M or particle numbers): each set keeps its own tables, work list
  * and dimension D_s, and each batched launch covers all sets.  Outputs are

@@ -676,7 +676,7 @@ class LowestEigenvalues:
 def solve_batch(hs, nev: int, q: int, max_basis: int, tol: float, precision: int = TRBL_PREC_F64,
                 keep: int = 0, max_iter: int = 0, check_every: int = 0, seed: int = 1, normH: float = 0.0,
                 want_vectors: bool = False, want_resid: bool = True, stream=None,
-                projections: int = TRBL_PROJ_TENSOR):
+                projections: int = TRBL_PROJ_TENSOR, reorth: int = TRBL_REORTH_SELECTIVE):
     """trbl_solve_batch over Hamiltonians on one basis or on bases of
     different dimension.  Returns (evals [nset, nev], resid [nset, nev] or
     None, vectors or None, per-set status, stats dict); vectors is a
@@ -685,7 +685,7 @@ def solve_batch(hs, nev: int, q: int, max_basis: int, tol: float, precision: int
     import torch
     nset = len(hs)
     dims = [h.basis.dim for h in hs]
-    p = _params(nev, q, max_basis, tol, precision, keep, max_iter, check_every, seed, normH, projections)
+    p = _params(nev, q, max_basis, tol, precision, keep, max_iter, check_every, seed, normH, projections, reorth)
     arr = (_VP * nset)(*[h.handle for h in hs])
     ev = np.zeros((nset, nev))
     rs = np.zeros((nset, nev)) if want_resid else None

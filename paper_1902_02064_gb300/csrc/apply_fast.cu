@@ -15,13 +15,8 @@
 // * the like-particle sources come as packed (offset, coefficient) pairs, one
 //   8-byte load per element: species A's are staged in shared memory per
 //   target, species B's are a table of (source row, coefficient) pairs;
-// * the cross term's staged proton jumps are (source offset, coefficient)
-//   pairs, one 8-byte shared-memory load per element, laid out per 2m
-//   transfer class as [neutron pair k][proton jump] with the class's own row
-//   length (the pair count of the opposite neutron class, 60 at most for the
-//   20-state space against a common maximum): a task reads a contiguous run
-//   of pairs, and the tables take less shared memory than rows of the
-//   common maximum length;
+// * the cross term's coefficient row is walked with a pointer increment and
+//   its source offsets are 32-bit shared-memory words;
 // * the q / 4 products of an element run as paired FP32 FMAs (fma.rn.f32x2),
 //   two lanes' worth of columns per instruction;
 // * the per-target staging runs on all warps: warp 0 forms the 2m-transfer
@@ -122,12 +117,12 @@ __device__ __forceinline__ void fast_body(const DevH<float>& h, const DevG<float
   constexpr int G = 32 / LPE;  // element groups per warp
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ND = h.ND;
-  const int maxQ = g.maxQ, maxK = g.maxK;
-  int2* pp = reinterpret_cast<int2*>(smem_raw);  // [maxQ] (offset of (pA, nB = 0), coefficient bits)
-  int2* pk = pp + maxQ;                          // [maxPK] (offset of (source pA, nB = 0), coefficient bits)
-  int* pstart = reinterpret_cast<int*>(pk + g.maxPK);  // [32] staged jumps by transfer class
-  int* cbase = pstart + 32;                            // [32] first pair of each class
-  int* nq = cbase + 32;                                // [1]
+  const int maxP = g.maxP, maxQ = g.maxQ, maxK = g.maxK;
+  int2* pp = reinterpret_cast<int2*>(smem_raw);            // [maxQ] (offset of (pA, nB = 0), coefficient bits)
+  int* pj = reinterpret_cast<int*>(pp + maxQ);             // [maxP + 1] offset of (source pA, nB = 0)
+  float* scoef = reinterpret_cast<float*>(pj + maxP + 1);  // [(maxP + 1) * maxK], proton sign folded in
+  int* pstart = reinterpret_cast<int*>(scoef + size_t(maxP + 1) * maxK);  // [32] staged jumps by transfer
+  int* nq = pstart + 32;                                                  // [1]
 
   const int4 item = g.work[item_index];
   const int pA = item.x, blk = item.y, r0 = item.z, nrows = item.w;
@@ -139,20 +134,16 @@ __device__ __forceinline__ void fast_body(const DevH<float>& h, const DevG<float
 
   // ---- stage the proton side of pA' ----
   if (warp == 0) {
-    int c = 0, w = 0;
-    if (lane < ND && h.srcblk[blk * ND + lane] >= 0) {
+    int c = 0;
+    if (lane < ND && h.srcblk[blk * ND + lane] >= 0)
       c = h.jsegA[int64_t(pA) * ND + lane + 1] - h.jsegA[int64_t(pA) * ND + lane];
-      w = c * g.kw[lane];
-    }
-    int s = c, sw = w;
+    int s = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int t = __shfl_up_sync(0xffffffffu, s, o);
-      const int tw = __shfl_up_sync(0xffffffffu, sw, o);
-      if (lane >= o) s += t, sw += tw;
+      if (lane >= o) s += t;
     }
-    pstart[lane] = s - c;  // lanes >= ND carry the totals (their counts are 0)
-    cbase[lane] = sw - w;
+    pstart[lane] = s - c;  // lanes >= ND carry the total (their count is 0)
     if (lane == 0) nq[0] = h.hoffA[pA + 1] - h.hoffA[pA];
   } else {
     const int q0 = h.hoffA[pA], Q = h.hoffA[pA + 1] - q0;
@@ -168,13 +159,12 @@ __device__ __forceinline__ void fast_body(const DevH<float>& h, const DevG<float
     const int soff = int(h.boff[sb]);
     const int snb = h.bnb[sb];
     const int e0 = h.jsegA[int64_t(pA) * ND + di];
-    int2* cls = pk + cbase[di];
-    const int n = cnt * g.kw[di];
-    for (int i = lane; i < n; i += 32) {
-      const int k = i / cnt, pi = i - k * cnt;  // pair k, proton jump pi
-      const int2 ja = h.jA[e0 + pi];
-      const float c = g.ccoef[size_t(ja.y >> 1) * maxK + k];
-      cls[i] = make_int2((soff + ja.x * snb) * ld, __float_as_int(c) ^ ((ja.y & 1) << 31));
+    for (int i = lane; i < cnt; i += 32) pj[ps + i] = (soff + h.jA[e0 + i].x * snb) * ld;
+    for (int i = lane; i < cnt * maxK; i += 32) {
+      const int pi = i / maxK, k = i - pi * maxK;
+      const int op = h.jA[e0 + pi].y;
+      const float c = g.ccoef[size_t(op >> 1) * maxK + k];
+      scoef[size_t(ps + pi) * maxK + k] = __int_as_float(__float_as_int(c) ^ ((op & 1) << 31));
     }
   }
   __syncthreads();
@@ -239,24 +229,26 @@ __device__ __forceinline__ void fast_body(const DevH<float>& h, const DevG<float
       for (int e = h.jsegB[int64_t(pB) * ND] + grp; e < e1; e += G) {
         const int2 jb = g.jB2[e];
         const int di = ND - 1 - ((jb.y >> 1) & 255);
-        const int cnt = pstart[di + 1] - pstart[di];
+        const int ps = pstart[di], pe = pstart[di + 1];
         const int neg = (jb.y & 1) << 31;
-        int p = cbase[di] + (jb.y >> 9) * cnt;  // pairs of neutron pair k, in jump order
-        const int pe = p + cnt;
+        const float* cp = scoef + size_t(ps) * maxK + (jb.y >> 9);
         const float* nsrc = Vl + jb.x * ld;
+        int p = ps;
         for (; p + 1 < pe; p += 2) {
-          const int2 u0 = pk[p], u1 = pk[p + 1];
+          const float c0 = __int_as_float(__float_as_int(cp[0]) ^ neg);
+          const float c1 = __int_as_float(__float_as_int(cp[maxK]) ^ neg);
+          cp += 2 * maxK;
           u64 a0, a1, b0, b1;
-          ldg16(nsrc + u0.x, a0, a1);
-          ldg16(nsrc + u1.x, b0, b1);
-          axpy4(acc, __int_as_float(u0.y ^ neg), a0, a1);
-          axpy4(acc, __int_as_float(u1.y ^ neg), b0, b1);
+          ldg16(nsrc + pj[p], a0, a1);
+          ldg16(nsrc + pj[p + 1], b0, b1);
+          axpy4(acc, c0, a0, a1);
+          axpy4(acc, c1, b0, b1);
         }
         if (p < pe) {
-          const int2 u0 = pk[p];
+          const float c0 = __int_as_float(__float_as_int(cp[0]) ^ neg);
           u64 a0, a1;
-          ldg16(nsrc + u0.x, a0, a1);
-          axpy4(acc, __int_as_float(u0.y ^ neg), a0, a1);
+          ldg16(nsrc + pj[p], a0, a1);
+          axpy4(acc, c0, a0, a1);
         }
         if (COMP) {
           racc.add(acc);
@@ -296,7 +288,9 @@ __global__ void __launch_bounds__(kThreads, MINB)
   fast_body<LPE, COMP>(h, g, blockIdx.x, Vs[blockIdx.y], ld, Ws[blockIdx.y], ldw);
 }
 
-size_t fast_smem(const DevG<float>& g) { return size_t(g.maxQ) * 8 + size_t(g.maxPK) * 8 + 65 * 4; }
+size_t fast_smem(const DevG<float>& g) {
+  return size_t(g.maxQ) * 8 + size_t(g.maxP + 1) * 4 + size_t(g.maxP + 1) * g.maxK * 4 + 33 * 4;
+}
 
 template <int LPE, int MINB, bool COMP>
 int launch_lpe(const DevH<float>& h, const DevG<float>& g, const float* V, int ld, float* W, int64_t ldw,

@@ -391,28 +391,19 @@ int upload_grouped(trbl_hamiltonian* h) {
     const int dn = B.twom[B.ja[e]] - B.twom[B.jc[e]] + span;
     jB2[e] = make_int2(loc, (k << 9) | (dn << 1) | (B.jsign[e] < 0 ? 1 : 0));
   }
-  // row length of a proton jump of class di: the pairs of the opposite
-  // neutron class (the p-n term couples transfers that cancel)
-  std::vector<int> kw(ND, 0);
-  for (int di = 0; di < ND; ++di) kw[di] = ncls[ND - 1 - di];
-  int maxP = 1, maxQ = 1, maxPK = 1;
+  int maxP = 1, maxQ = 1;
   const int nblk = int(b->blocks.size());
   for (int k = 0; k < nblk; ++k) {
     const Block& bl = b->blocks[k];
     const int a0 = A.gfirst[bl.gA];
     for (int ia = 0; ia < bl.na; ++ia) {
       const int pA = a0 + ia;
-      int P = 0, PK = 0;
+      int P = 0;
       for (int di = 0; di < ND; ++di)
-        if (b->srcblk[size_t(k) * ND + di] >= 0) {
-          const int c = A.jseg[size_t(pA) * ND + di + 1] - A.jseg[size_t(pA) * ND + di];
-          P += c;
-          PK += c * kw[di];
-        }
+        if (b->srcblk[size_t(k) * ND + di] >= 0) P += A.jseg[size_t(pA) * ND + di + 1] - A.jseg[size_t(pA) * ND + di];
       const int Q = h->hoff[0][pA + 1] - h->hoff[0][pA];
       maxP = std::max(maxP, P);
       maxQ = std::max(maxQ, Q);
-      maxPK = std::max(maxPK, PK);
     }
   }
   const size_t sm64 = smem_bytes(maxP, maxQ, maxK, ND, 8);
@@ -433,8 +424,7 @@ int upload_grouped(trbl_hamiltonian* h) {
   size_t o_c64 = (o_jB2 + jB2.size() * sizeof(int2) + 255) & ~size_t(255);
   size_t o_c32 = (o_c64 + cc.size() * 8 + 255) & ~size_t(255);
   size_t o_lB = (o_c32 + cc32.size() * 4 + 255) & ~size_t(255);
-  size_t o_kw = (o_lB + likeB.size() * sizeof(int2) + 255) & ~size_t(255);
-  size_t total = o_kw + kw.size() * sizeof(int) + 256;
+  size_t total = o_lB + likeB.size() * sizeof(int2) + 256;
   void* arena = nullptr;
   TRBL_CUDA(cudaMalloc(&arena, total));
   h->garena = arena;
@@ -444,14 +434,11 @@ int upload_grouped(trbl_hamiltonian* h) {
   TRBL_CUDA(cudaMemcpy(base + o_c32, cc32.data(), cc32.size() * 4, cudaMemcpyHostToDevice));
   if (!likeB.empty())
     TRBL_CUDA(cudaMemcpy(base + o_lB, likeB.data(), likeB.size() * sizeof(int2), cudaMemcpyHostToDevice));
-  TRBL_CUDA(cudaMemcpy(base + o_kw, kw.data(), kw.size() * sizeof(int), cudaMemcpyHostToDevice));
   auto fill = [&](auto& g, size_t o_c) {
     using TT = typename std::remove_const<typename std::remove_pointer<decltype(g.ccoef)>::type>::type;
     g.maxP = maxP;
     g.maxQ = maxQ;
     g.maxK = maxK;
-    g.maxPK = maxPK;
-    g.kw = reinterpret_cast<const int*>(base + o_kw);
     g.jB2 = reinterpret_cast<const int2*>(base + o_jB2);
     g.ccoef = reinterpret_cast<const TT*>(base + o_c);
   };

@@ -112,7 +112,9 @@ __global__ void __launch_bounds__(32 * (QP / 4)) block_dot_kernel(
 template <typename T, int QP>
 __global__ void __launch_bounds__(32 * (QP / 4)) block_dot_batched_kernel(
     const T* const* __restrict__ Bs_, int64_t ldb, int m, const T* const* __restrict__ Ws_, int64_t ldw, int q,
-    const int64_t* __restrict__ Ds, int64_t rows_per_chunk, double* const* __restrict__ partials) {
+    const int64_t* __restrict__ Ds, int64_t rows_per_chunk, double* const* __restrict__ partials,
+    const int* __restrict__ skip) {
+  if (skip && skip[blockIdx.z]) return;
   const int64_t D = Ds[blockIdx.z];
   const T* __restrict__ B = Bs_[blockIdx.z];
   const T* __restrict__ W = Ws_[blockIdx.z];
@@ -178,9 +180,9 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partial, int n
 }
 
 __global__ void reduce_partials_batched_kernel(double* const* __restrict__ partial, int nchunk, int mq,
-                                               double* const* __restrict__ C) {
+                                               double* const* __restrict__ C, const int* __restrict__ skip) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= mq) return;
+  if (i >= mq || (skip && skip[blockIdx.y])) return;
   const double* P = partial[blockIdx.y];
   double s = 0.0;
   for (int c = 0; c < nchunk; ++c) s += P[int64_t(c) * mq + i];
@@ -245,7 +247,9 @@ __global__ void __launch_bounds__(RT * CT / 16) rowgemm_kernel(
 template <typename T, int RT, int CT>
 __global__ void __launch_bounds__(RT * CT / 16) rowgemm_batched_kernel(
     const T* const* __restrict__ Ins, int64_t ldi, int K, const double* const* __restrict__ Us_, int64_t ldu, int n,
-    T* const* __restrict__ Outs, int64_t ldo, const int64_t* __restrict__ Ds, double alpha, double beta) {
+    T* const* __restrict__ Outs, int64_t ldo, const int64_t* __restrict__ Ds, double alpha, double beta,
+    const int* __restrict__ skip) {
+  if (skip && skip[blockIdx.z]) return;
   const int64_t D = Ds[blockIdx.z];
   if (int64_t(blockIdx.x) * RT >= D) return;
   const T* __restrict__ In = Ins[blockIdx.z];
@@ -609,7 +613,7 @@ void reduce_partials(const double* partial, int nchunk, int mq, double* C, cudaS
 template <typename T>
 int block_dot_batched(const T* const* B, int64_t ldb, int m, const T* const* W, int64_t ldw, int q,
                       const int64_t* Ds, int64_t D, double* const* C, double* const* partial, size_t partial_bytes,
-                      int nset, cudaStream_t s) {
+                      int nset, cudaStream_t s, const int* skip) {
   if (m <= 0 || nset <= 0 || D <= 0) return TRBL_OK;
   constexpr int RS = DotCfg<T>::RS;
   const int mtiles = (m + MT - 1) / MT;
@@ -623,7 +627,7 @@ int block_dot_batched(const T* const* B, int64_t ldb, int m, const T* const* W, 
   nchunk = (D + rows - 1) / rows;
   const dim3 grid{unsigned(mtiles), unsigned(nchunk), unsigned(nset)};
 #define TRBL_BDOT(QP) \
-  block_dot_batched_kernel<T, QP><<<grid, 32 * (QP / 4), 0, s>>>(B, ldb, m, W, ldw, q, Ds, rows, partial)
+  block_dot_batched_kernel<T, QP><<<grid, 32 * (QP / 4), 0, s>>>(B, ldb, m, W, ldw, q, Ds, rows, partial, skip)
   if (q <= 4) TRBL_BDOT(4);
   else if (q <= 8) TRBL_BDOT(8);
   else if (q <= 16) TRBL_BDOT(16);
@@ -635,7 +639,7 @@ int block_dot_batched(const T* const* B, int64_t ldb, int m, const T* const* W, 
   TRBL_CUDA(cudaGetLastError());
   const int mq = m * q;
   const dim3 rgrid{unsigned((mq + 255) / 256), unsigned(nset), 1u};
-  reduce_partials_batched_kernel<<<rgrid, 256, 0, s>>>(partial, int(nchunk), mq, C); note_launch();
+  reduce_partials_batched_kernel<<<rgrid, 256, 0, s>>>(partial, int(nchunk), mq, C, skip); note_launch();
   TRBL_CUDA(cudaGetLastError());
   return TRBL_OK;
 }
@@ -643,20 +647,23 @@ int block_dot_batched(const T* const* B, int64_t ldb, int m, const T* const* W, 
 template <typename T>
 int rowgemm_batched(const T* const* In, int64_t ldi, int K, const double* const* U, int64_t ldu, int n,
                     T* const* Out, int64_t ldo, const int64_t* Ds, int64_t D, double alpha, double beta, int nset,
-                    cudaStream_t s) {
+                    cudaStream_t s, const int* skip) {
   if (n <= 0 || D <= 0 || K <= 0 || nset <= 0) return TRBL_OK;
   if (n <= 16) {
     constexpr int RT = 128, CT = 16;
     const dim3 grid{unsigned((D + RT - 1) / RT), unsigned((n + CT - 1) / CT), unsigned(nset)};
-    rowgemm_batched_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, Ds, alpha, beta);
+    rowgemm_batched_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, Ds, alpha, beta,
+                                                                                 skip);
   } else if (n <= 32) {
     constexpr int RT = 128, CT = 32;
     const dim3 grid{unsigned((D + RT - 1) / RT), unsigned((n + CT - 1) / CT), unsigned(nset)};
-    rowgemm_batched_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, Ds, alpha, beta);
+    rowgemm_batched_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, Ds, alpha, beta,
+                                                                                 skip);
   } else {
     constexpr int RT = 64, CT = 64;
     const dim3 grid{unsigned((D + RT - 1) / RT), unsigned((n + CT - 1) / CT), unsigned(nset)};
-    rowgemm_batched_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, Ds, alpha, beta);
+    rowgemm_batched_kernel<T, RT, CT><<<grid, RT * CT / 16, 0, s>>>(In, ldi, K, U, ldu, n, Out, ldo, Ds, alpha, beta,
+                                                                                 skip);
   }
   note_launch();
   TRBL_CUDA(cudaGetLastError());
@@ -665,16 +672,16 @@ int rowgemm_batched(const T* const* In, int64_t ldi, int K, const double* const*
 
 template int block_dot_batched<float>(const float* const*, int64_t, int, const float* const*, int64_t, int,
                                       const int64_t*, int64_t, double* const*, double* const*, size_t, int,
-                                      cudaStream_t);
+                                      cudaStream_t, const int*);
 template int block_dot_batched<double>(const double* const*, int64_t, int, const double* const*, int64_t, int,
                                        const int64_t*, int64_t, double* const*, double* const*, size_t, int,
-                                       cudaStream_t);
+                                       cudaStream_t, const int*);
 template int rowgemm_batched<float>(const float* const*, int64_t, int, const double* const*, int64_t, int,
                                     float* const*, int64_t, const int64_t*, int64_t, double, double, int,
-                                    cudaStream_t);
+                                    cudaStream_t, const int*);
 template int rowgemm_batched<double>(const double* const*, int64_t, int, const double* const*, int64_t, int,
                                      double* const*, int64_t, const int64_t*, int64_t, double, double, int,
-                                     cudaStream_t);
+                                     cudaStream_t, const int*);
 
 template <typename T>
 int block_dot_capped(const T* B, int64_t ldb, int m, const T* W, int64_t ldw, int q, int64_t D, double* C,
@@ -1036,6 +1043,53 @@ int gram_f32_launch(const float* W, int64_t ldw, int64_t D, double* G, Workspace
   return TRBL_OK;
 }
 
+// col_sumsq_kernel over several problems: grid y = problem; a block whose
+// row range lies past its problem's rows writes zeros.
+template <typename T>
+__global__ void col_sumsq_batched_kernel(const T* const* __restrict__ Ws, int64_t ldw, int q,
+                                         const int64_t* __restrict__ Ds, int64_t rows_per_block,
+                                         double* const* __restrict__ partials) {
+  __shared__ double red[256];
+  const T* __restrict__ W = Ws[blockIdx.y];
+  const int64_t D = Ds[blockIdx.y];
+  const int t = threadIdx.x;
+  const int per = blockDim.x / q;
+  const int c = t % q, rl = t / q;
+  double acc = 0.0;
+  if (rl < per) {
+    const int64_t r0 = int64_t(blockIdx.x) * rows_per_block;
+    const int64_t r1 = r0 + rows_per_block < D ? r0 + rows_per_block : D;
+    for (int64_t r = r0 + rl; r < r1; r += per) {
+      const double x = double(W[r * ldw + c]);
+      acc = fma(x, x, acc);
+    }
+  }
+  red[t] = acc;
+  __syncthreads();
+  if (t < q) {
+    double v = 0.0;
+    for (int k = 0; k < per; ++k) v += red[k * q + t];
+    partials[blockIdx.y][int64_t(blockIdx.x) * q + t] = v;
+  }
+}
+
+template <typename T>
+int col_sumsq_batched(const T* const* W, int64_t ldw, int q, const int64_t* Ds, int64_t D, double* const* out,
+                      double* const* partial, size_t partial_bytes, int sm_count, int nset, cudaStream_t s) {
+  if (q <= 0 || q > 256 || D <= 0 || nset <= 0) return fail(TRBL_ERR_ARG, "col_sumsq_batched: q=%d", q);
+  int64_t nblk = std::min<int64_t>(std::max(1, (4 * sm_count + nset - 1) / nset), (D + 255) / 256);
+  nblk = std::max<int64_t>(1, std::min<int64_t>(nblk, int64_t(partial_bytes / (sizeof(double) * q))));
+  const int64_t rows = (D + nblk - 1) / nblk;
+  nblk = (D + rows - 1) / rows;
+  const dim3 grid{unsigned(nblk), unsigned(nset), 1u};
+  col_sumsq_batched_kernel<T><<<grid, 256, 0, s>>>(W, ldw, q, Ds, rows, partial); note_launch();
+  TRBL_CUDA(cudaGetLastError());
+  const dim3 rgrid{unsigned((q + 255) / 256), unsigned(nset), 1u};
+  reduce_partials_batched_kernel<<<rgrid, 256, 0, s>>>(partial, int(nblk), q, out, nullptr); note_launch();
+  TRBL_CUDA(cudaGetLastError());
+  return TRBL_OK;
+}
+
 template <typename T>
 int col_sumsq(const T* W, int64_t ldw, int q, int64_t D, double* out, Workspace& ws, cudaStream_t s) {
   if (q <= 0 || q > 256 || D <= 0) return fail(TRBL_ERR_ARG, "col_sumsq: q=%d D=%lld", q, (long long)D);
@@ -1102,6 +1156,10 @@ template int rowgemm<double>(const double*, int64_t, int, const double*, int64_t
 template int rowgemm_ws<float>(const float*, int64_t, int, const double*, int64_t, int, float*, int64_t, int64_t, double, double, Workspace&, cudaStream_t);
 template int col_sumsq<float>(const float*, int64_t, int, int64_t, double*, Workspace&, cudaStream_t);
 template int gram<float>(const float*, int64_t, int, int64_t, double*, Workspace&, cudaStream_t);
+template int col_sumsq_batched<float>(const float* const*, int64_t, int, const int64_t*, int64_t, double* const*,
+                                      double* const*, size_t, int, int, cudaStream_t);
+template int col_sumsq_batched<double>(const double* const*, int64_t, int, const int64_t*, int64_t, double* const*,
+                                       double* const*, size_t, int, int, cudaStream_t);
 template int gram<double>(const double*, int64_t, int, int64_t, double*, Workspace&, cudaStream_t);
 template int col_sumsq<double>(const double*, int64_t, int, int64_t, double*, Workspace&, cudaStream_t);
 template int rowgemm_ws<double>(const double*, int64_t, int, const double*, int64_t, int, double*, int64_t, int64_t, double, double, Workspace&, cudaStream_t);

@@ -96,14 +96,21 @@ int wide_error_to_host(int* host, cudaStream_t s);
 // device arrays of pointers and has Ds[s] rows (device array; D = the
 // largest, which sizes the grid).  block_dot_batched uses about 1,024 rows
 // per thread block so that many small problems fill the GPU together.
+// skip (device array, or null): problem s does nothing when skip[s] != 0
+// (its outputs keep their contents).
 template <typename T>
 int block_dot_batched(const T* const* B, int64_t ldb, int m, const T* const* W, int64_t ldw, int q,
                       const int64_t* Ds, int64_t D, double* const* C, double* const* partial, size_t partial_bytes,
-                      int nset, cudaStream_t s);
+                      int nset, cudaStream_t s, const int* skip = nullptr);
 template <typename T>
 int rowgemm_batched(const T* const* In, int64_t ldi, int K, const double* const* U, int64_t ldu, int n,
                     T* const* Out, int64_t ldo, const int64_t* Ds, int64_t D, double alpha, double beta, int nset,
-                    cudaStream_t s);
+                    cudaStream_t s, const int* skip = nullptr);
+// out[s][c] = sum_r W[s][r][c]^2 over the Ds[s] rows of problem s (q <= 256),
+// deterministic; partial[s] needs (4 x SMs) x q doubles.
+template <typename T>
+int col_sumsq_batched(const T* const* W, int64_t ldw, int q, const int64_t* Ds, int64_t D, double* const* out,
+                      double* const* partial, size_t partial_bytes, int sm_count, int nset, cudaStream_t s);
 
 // dst[:, 0:ncol] = src[:, 0:ncol] (with type conversion).
 template <typename S, typename T>

@@ -100,9 +100,6 @@ struct DevG {
   const int2* jB2;      // neutron jumps: (source local index, (k << 9) | (transfer << 1) | negative), k = pair index in its 2m-transfer class
   const T* ccoef;       // ccoef[(a*nA + c) * maxK + k] = V^AB_{a b_k, c d_k} for the class of transfer m_c - m_a
   const int2* likeB;    // FP32 tables only: species-B like-particle rows as (source local index, FP32 coefficient bits)
-  const int* kw;        // [ND] coefficient row length of the proton jumps of transfer class di (the opposite
-                        // neutron class's pair count)
-  int maxPK;            // per-target sum over the staged proton jumps of their row lengths
 };
 
 }  // namespace trbl

@@ -334,6 +334,47 @@ __global__ void set_alpha_batched_kernel(const SetPtrs<T>* __restrict__ sp, int 
   p.Tm[int64_t(b0 + r) * ldt + b0 + c] = 0.5 * (p.C[(b0 + r) * q + c] + p.C[(b0 + c) * q + r]);
 }
 
+// Selective reorthogonalisation of a batch: dst[s] = src[s] + off (the
+// local window's first column in every set's basis)
+template <typename T>
+__global__ void offset_ptrs_kernel(T* const* __restrict__ src, int64_t off, T** __restrict__ dst, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i] + off;
+}
+
+// The DGKS test per set: skip[s] = 0 (run the second full pass) when a
+// column of W kept at most half its squared norm through the first (G's
+// diagonal after, nb before; NaN runs it too), else 1.
+__global__ void dgks_flags_kernel(const double* const* __restrict__ G, const double* const* __restrict__ nb, int q,
+                                  int* __restrict__ skip, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int again = 0;
+  for (int j = 0; j < q; ++j)
+    if (!(G[i][j * q + j] > 0.5 * nb[i][j])) again = 1;
+  skip[i] = again ? 0 : 1;
+}
+
+// alpha of the selective pass: the projection on V_k summed over the local
+// pass (Cl rows ql - q ..), the full pass (C) and, where it ran, the second
+// (C + ldt q); symmetrised into T_s as set_alpha_batched_kernel does
+template <typename T>
+__global__ void set_alpha_sel_batched_kernel(const SetPtrs<T>* __restrict__ sp, double* const* __restrict__ Cl,
+                                             const int* __restrict__ skip, int ldt, int b0, int ql, int q) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= q * q) return;
+  const SetPtrs<T> p = sp[blockIdx.y];
+  const double* cl = Cl[blockIdx.y];
+  const bool two = skip[blockIdx.y] == 0;
+  const int r = i / q, c = i - r * q;
+  auto a = [&](int x, int y) {
+    double v = cl[(ql - q + x) * q + y] + p.C[(b0 + x) * q + y];
+    if (two) v += p.C[size_t(ldt) * q + (b0 + x) * q + y];
+    return v;
+  };
+  p.Tm[int64_t(b0 + r) * ldt + b0 + c] = 0.5 * (a(r, c) + a(c, r));
+}
+
 // grid (., sets): beta_s = R2_s R1_s, then its two copies in T_s
 template <typename T>
 __global__ void beta_batched_kernel(const SetPtrs<T>* __restrict__ sp, int ldt, int r0, int c0, int q, int set_t) {
@@ -1213,6 +1254,11 @@ struct BatchDriver {
   double** P_R1i = nullptr;
   double** P_R2i = nullptr;
   double** P_part = nullptr;
+  T** P_Bl = nullptr;      // selective pass: the local window of each basis (written in the step)
+  double** P_Cl = nullptr;  // selective pass: local coefficients
+  double** P_Gn = nullptr;  // selective pass: squared column norms before the full pass
+  int* dskip = nullptr;     // selective pass: 1 where a set skips the second full pass
+  int64_t second_passes = 0;
   SetPtrs<T>* dsp = nullptr;
   int* dcounts = nullptr;
   SetPtrs<T>* hsp = nullptr;  // pinned: the records, thresholds refreshed before each step
@@ -1368,11 +1414,11 @@ struct BatchDriver {
   // Device arrays of the sets' pointers for the batched step.
   int setup_pointers() {
     const size_t np = size_t(nset);
-    const size_t bytes = np * (4 * sizeof(T*) + 6 * sizeof(double*)) + np * sizeof(SetPtrs<T>) + 2 * np * sizeof(int) +
+    const size_t bytes = np * (5 * sizeof(T*) + 8 * sizeof(double*)) + np * sizeof(SetPtrs<T>) + 3 * np * sizeof(int) +
                          np * sizeof(int64_t) + 512;
     TRBL_CUDA(cudaMalloc(&bptr, bytes));
     TRBL_CUDA(cudaMallocHost(&hsp, np * sizeof(SetPtrs<T>)));
-    TRBL_CUDA(cudaMallocHost(&hcounts, (2 * np + 4) * sizeof(int)));
+    TRBL_CUDA(cudaMallocHost(&hcounts, (3 * np + 4) * sizeof(int)));
     std::vector<char> host(bytes);
     size_t off = 0;
     auto place = [&](auto** dev, auto f) {
@@ -1392,6 +1438,9 @@ struct BatchDriver {
     place(&P_R1i, [](Solver<T>& S) { return S.R1i; });
     place(&P_R2i, [](Solver<T>& S) { return S.R2i; });
     place(&P_part, [](Solver<T>& S) { return S.ws.partial; });
+    place(&P_Bl, [](Solver<T>& S) { return S.basis; });
+    place(&P_Cl, [](Solver<T>& S) { return S.Cl; });
+    place(&P_Gn, [](Solver<T>& S) { return S.Gn; });
     off = (off + 15) & ~size_t(15);
     dsp = reinterpret_cast<SetPtrs<T>*>(static_cast<char*>(bptr) + off);
     for (int i = 0; i < nset; ++i) {
@@ -1404,13 +1453,16 @@ struct BatchDriver {
     std::memcpy(host.data() + off, Ds.data(), np * sizeof(int64_t));
     off += np * sizeof(int64_t);
     dcounts = reinterpret_cast<int*>(static_cast<char*>(bptr) + off);
+    off += 2 * np * sizeof(int);
+    dskip = reinterpret_cast<int*>(static_cast<char*>(bptr) + off);
+    std::memset(host.data() + off, 0, np * sizeof(int));
     part_bytes = sets[0]->ws.partial_bytes;
     TRBL_CUDA(cudaMemcpy(bptr, host.data(), bytes, cudaMemcpyHostToDevice));
     return TRBL_OK;
   }
 
-  // One block step of every set (Alg. 4 after the product): CGS2 against
-  // each basis, alpha into T, Cholesky QR twice, beta and the append of
+  // One block step of every set (Alg. 4 after the product): the selective
+  // reorthogonalisation (or CGS2 with TRBL_REORTH_TWICE) against each basis, alpha into T, Cholesky QR twice, beta and the append of
   // V_{k+1}, each a single launch over all sets; then the deficiency counts
   // and wait-timeout words to pinned host memory.
   int enqueue(bool append) {
@@ -1426,13 +1478,35 @@ struct BatchDriver {
     const T* const* cB = P_basis;
     const T* const* cW = P_W;
     const T* const* cW2 = P_W2;
-    TRY(block_dot_batched<T>(cB, mb, nb, cW, q, q, P_D, D, P_C1, P_part, part_bytes, nset, s));
-    TRY(rowgemm_batched<T>(cB, mb, nb, P_C1, q, q, P_W, q, P_D, D, -1.0, 1.0, nset, s));
-    TRY(block_dot_batched<T>(cB, mb, nb, cW, q, q, P_D, D, P_C2, P_part, part_bytes, nset, s));
-    TRY(rowgemm_batched<T>(cB, mb, nb, P_C2, q, q, P_W, q, P_D, D, -1.0, 1.0, nset, s));
     const dim3 gq{unsigned((q * q + 127) / 128), unsigned(nset), 1u};
-    set_alpha_batched_kernel<T><<<gq, 128, 0, s>>>(dsp, mb, nb - q, q); note_launch();
-    TRY(block_dot_batched<T>(cW, q, q, cW, q, q, P_D, D, P_G, P_part, part_bytes, nset, s));
+    if (prm.reorth == TRBL_REORTH_TWICE) {
+      TRY(block_dot_batched<T>(cB, mb, nb, cW, q, q, P_D, D, P_C1, P_part, part_bytes, nset, s));
+      TRY(rowgemm_batched<T>(cB, mb, nb, P_C1, q, q, P_W, q, P_D, D, -1.0, 1.0, nset, s));
+      TRY(block_dot_batched<T>(cB, mb, nb, cW, q, q, P_D, D, P_C2, P_part, part_bytes, nset, s));
+      TRY(rowgemm_batched<T>(cB, mb, nb, P_C2, q, q, P_W, q, P_D, D, -1.0, 1.0, nset, s));
+      set_alpha_batched_kernel<T><<<gq, 128, 0, s>>>(dsp, mb, nb - q, q); note_launch();
+      TRY(block_dot_batched<T>(cW, q, q, cW, q, q, P_D, D, P_G, P_part, part_bytes, nset, s));
+    } else {
+      // the single solver's selective pass, with the DGKS decision taken on
+      // the device: the second full pass (and the Gram matrix after it) runs
+      // for the sets whose flag asks for it, the others return at once
+      constexpr int kAlign = int(16 / sizeof(T));
+      const int c0 = std::max(0, nb - 2 * q) / kAlign * kAlign;
+      const int ql = nb - c0;
+      offset_ptrs_kernel<T><<<(nset + 127) / 128, 128, 0, s>>>(P_basis, c0, P_Bl, nset); note_launch();
+      const T* const* cBl = P_Bl;
+      TRY(block_dot_batched<T>(cBl, mb, ql, cW, q, q, P_D, D, P_Cl, P_part, part_bytes, nset, s));
+      TRY(rowgemm_batched<T>(cBl, mb, ql, P_Cl, q, q, P_W, q, P_D, D, -1.0, 1.0, nset, s));
+      TRY(col_sumsq_batched<T>(cW, q, q, P_D, D, P_Gn, P_part, part_bytes, sets[0]->ws.sm_count, nset, s));
+      TRY(block_dot_batched<T>(cB, mb, nb, cW, q, q, P_D, D, P_C1, P_part, part_bytes, nset, s));
+      TRY(rowgemm_batched<T>(cB, mb, nb, P_C1, q, q, P_W, q, P_D, D, -1.0, 1.0, nset, s));
+      TRY(block_dot_batched<T>(cW, q, q, cW, q, q, P_D, D, P_G, P_part, part_bytes, nset, s));
+      dgks_flags_kernel<<<(nset + 127) / 128, 128, 0, s>>>(P_G, P_Gn, q, dskip, nset); note_launch();
+      TRY(block_dot_batched<T>(cB, mb, nb, cW, q, q, P_D, D, P_C2, P_part, part_bytes, nset, s, dskip));
+      TRY(rowgemm_batched<T>(cB, mb, nb, P_C2, q, q, P_W, q, P_D, D, -1.0, 1.0, nset, s, dskip));
+      TRY(block_dot_batched<T>(cW, q, q, cW, q, q, P_D, D, P_G, P_part, part_bytes, nset, s, dskip));
+      set_alpha_sel_batched_kernel<T><<<gq, 128, 0, s>>>(dsp, P_Cl, dskip, mb, nb - q, ql, q); note_launch();
+    }
     chol_batched_kernel<T><<<nset, 64, 0, s>>>(dsp, q, 1, 0.0, sets[0]->tau_max); note_launch();
     TRY(rowgemm_batched<T>(cW, q, q, P_R1i, q, q, P_W2, q, P_D, D, 1.0, 0.0, nset, s));
     TRY(block_dot_batched<T>(cW2, q, q, cW2, q, q, P_D, D, P_G, P_part, part_bytes, nset, s));
@@ -1446,6 +1520,7 @@ struct BatchDriver {
     gather_counts_kernel<T><<<(nset + 127) / 128, 128, 0, s>>>(dsp, nset, dcounts); note_launch();
     TRBL_CUDA(cudaGetLastError());
     TRBL_CUDA(cudaMemcpyAsync(hcounts, dcounts, sizeof(int) * 2 * nset, cudaMemcpyDeviceToHost, s));
+    TRBL_CUDA(cudaMemcpyAsync(hcounts + 2 * nset + 4, dskip, sizeof(int) * nset, cudaMemcpyDeviceToHost, s));
     TRY(tma_error_to_host(hcounts + 2 * nset, s));
     TRY(dot_error_to_host(hcounts + 2 * nset + 1, s));
     TRY(tc_error_to_host(hcounts + 2 * nset + 2, s));
@@ -1512,6 +1587,7 @@ struct BatchDriver {
         hf[kF1] = hcounts[2 * i];
         hf[kF2] = hcounts[2 * i + 1];
         for (int k = 0; k < 4; ++k) hf[kTmaErr + k] = hcounts[2 * nset + k];
+        if (prm.reorth != TRBL_REORTH_TWICE && hcounts[2 * nset + 4 + i] == 0) ++second_passes;
       }
       const double t_step = ms_since(t0);
       ms_steps += t_step;
@@ -1567,6 +1643,7 @@ struct BatchDriver {
       st->ms_total = ms_since(t_start);
       st->ms_apply = ms_steps;
       st->ms_ritz = ms_between;
+      st->second_passes = int(std::min<int64_t>(second_passes, 0x7fffffff));
     }
     trace("batch: %d steps, steps %.1f ms, between %.1f ms, total %.1f ms", it, ms_steps, ms_between,
           ms_since(t_start));
@@ -1636,15 +1713,33 @@ extern "C" int trbl_solver_step_host(trbl_solver* sv, const void* block_in, void
   clear_error();
   if (!sv || !sv->impl) return fail(TRBL_ERR_ARG, "null solver");
   const size_t bytes = sv->impl->block_bytes();
+  // with TRBL_TRACE=1, the two copies are timed with events on the stream
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (trace_on())
+    for (auto& e : ev) cudaEventCreate(&e);
+  if (ev[0]) cudaEventRecord(ev[0], sv->stream);
   if (block_in)
     TRBL_CUDA(cudaMemcpyAsync(sv->impl->block(), block_in, bytes, cudaMemcpyHostToDevice, sv->stream));
+  if (ev[1]) cudaEventRecord(ev[1], sv->stream);
   int rc = sv->impl->step(converged);
-  if (rc) return rc;
-  if (block_out) {
-    TRBL_CUDA(cudaMemcpyAsync(block_out, sv->impl->block(), bytes, cudaMemcpyDeviceToHost, sv->stream));
-    TRBL_CUDA(cudaStreamSynchronize(sv->stream));
+  if (rc == TRBL_OK && block_out) {
+    if (ev[2]) cudaEventRecord(ev[2], sv->stream);
+    rc = cudaMemcpyAsync(block_out, sv->impl->block(), bytes, cudaMemcpyDeviceToHost, sv->stream) == cudaSuccess
+             ? TRBL_OK
+             : fail(TRBL_ERR_CUDA, "cudaMemcpyAsync (block out)");
+    if (ev[3]) cudaEventRecord(ev[3], sv->stream);
+    if (rc == TRBL_OK && cudaStreamSynchronize(sv->stream) != cudaSuccess)
+      rc = fail(TRBL_ERR_CUDA, "cudaStreamSynchronize (block out)");
   }
-  return TRBL_OK;
+  if (ev[0]) {
+    cudaStreamSynchronize(sv->stream);
+    float in_ms = 0.f, out_ms = 0.f;
+    cudaEventElapsedTime(&in_ms, ev[0], ev[1]);
+    if (block_out && rc == TRBL_OK) cudaEventElapsedTime(&out_ms, ev[2], ev[3]);
+    trace("step_host: copy in %.2f ms, copy out %.2f ms (%zu bytes each)", in_ms, out_ms, bytes);
+    for (auto& e : ev) cudaEventDestroy(e);
+  }
+  return rc;
 }
 
 extern "C" int trbl_solver_state_bytes(trbl_solver* sv, int64_t* bytes) {

@@ -28,12 +28,16 @@ def _sets(kA, kB, seeds):
     return sp, tb, inters, hs
 
 
+@pytest.mark.parametrize("reorth", [trbl.TRBL_REORTH_SELECTIVE, trbl.TRBL_REORTH_TWICE])
 @pytest.mark.parametrize("precision,tol,bar", [(trbl.TRBL_PREC_F64, 1e-10, 1e-9), (trbl.TRBL_PREC_MIXED, 1e-6, 1e-6)])
-def test_batch_small_against_dense(precision, tol, bar):
+def test_batch_small_against_dense(precision, tol, bar, reorth):
+    """Both reorthogonalisation schedules of the batched step (the selective
+    one takes its DGKS decision per set on the device)."""
     seeds = list(range(200, 208))
     sp, tb, inters, hs = _sets(2, 2, seeds)
     B = ob.ProductBasis(sp.twom, 2, sp.twom, 2, 0)
-    ev, rs, X, status, st = trbl.solve_batch(hs, 10, 4, 40, tol, precision=precision, want_vectors=True)
+    ev, rs, X, status, st = trbl.solve_batch(hs, 10, 4, 40, tol, precision=precision, want_vectors=True,
+                                             reorth=reorth)
     assert st["rc"] == trbl.TRBL_OK, st["message"]
     assert status == [0] * len(seeds)
     for k, it in enumerate(inters):
