@@ -175,21 +175,22 @@ def measured_peaks():
         return None
 
 
-def ncu_traffic(rows_per_item=128, path=os.path.join(ROOT, "profiles", "apply_traffic.json")):
+def ncu_traffic(kernel, rows_per_item, path=os.path.join(ROOT, "profiles", "apply_traffic.json")):
     """(DRAM bytes per apply launch, kernel name) from a committed ncu summary.
-    The bytes are None unless the summary was taken on the kernel source as it
-    is now (its SHA-256 is stored beside the figure) and with the same launch
-    shape (neutron rows per work item)."""
+    The bytes are None unless the summary was taken on the same kernel, on its
+    source file as it is now (its SHA-256 is stored beside the figure) and
+    with the same launch shape (neutron rows per work item)."""
     try:
         d = json.load(open(path))
     except (OSError, ValueError):
         return None, None
-    src = os.path.join(ROOT, "paper_1902_02064_gb300", "csrc", "apply_grouped.cu")
+    name = "apply_fast.cu" if kernel.startswith("apply_fast") else "apply_grouped.cu"
+    src = os.path.join(ROOT, "paper_1902_02064_gb300", "csrc", name)
     try:
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except OSError:
         sha = None
-    if d.get("source_sha256") != sha or d.get("rows_per_item", 128) != rows_per_item:
+    if d.get("kernel") != kernel or d.get("source_sha256") != sha or d.get("rows_per_item", 128) != rows_per_item:
         return None, d.get("kernel")
     return d.get("dram_bytes_per_launch_full_size"), d.get("kernel")
 
@@ -469,7 +470,9 @@ def run_ours(args, rank, world):
     value = job_throughput(nnz * q * args.steps, ms * 1e-3, world) / 1e9
     ms_apply = (st1["ms_apply"] - st0["ms_apply"]) / args.steps
     achieved = b_slab / (ms_apply * 1e-3) / 1e9
-    traffic, _ = ncu_traffic(tune_rows)
+    kname = {0: "apply_grouped_kernel<float, 8, 1>", 2: "apply_grouped_kernel<float, 4, 2>"}.get(
+        shape[0], "apply_fast_kernel<8, %d, false>" % shape[2])
+    traffic, _ = ncu_traffic(kname, tune_rows)
 
     # end to end: the same block steps as the device-timed region (a fresh
     # solver through the same set-up and warm-up, whose last step fills the
@@ -497,6 +500,8 @@ def run_ours(args, rank, world):
     se1 = sv.stats()
     e2e_value = job_throughput(nnz * q * args.steps, el, world) / 1e9
     e2e_phase_ms = sum(se1[k] - se0[k] for k in ("ms_apply", "ms_orth", "ms_qr", "ms_ritz", "ms_restart"))
+    copy_in_ms = (se1["ms_copy_in"] - se0["ms_copy_in"]) / args.steps
+    copy_out_ms = (se1["ms_copy_out"] - se0["ms_copy_out"]) / args.steps
     copy_ms = el * 1e3 - e2e_phase_ms
     numa = host_in.numa_node
     host_in.free()
@@ -531,8 +536,7 @@ def run_ours(args, rank, world):
         "second_reorth_passes_in_timed_steps": st1["second_passes"] - st0["second_passes"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": {0: "apply_grouped_kernel<float, 8, 1>", 2: "apply_grouped_kernel<float, 4, 2>"}.get(
-                         shape[0], "apply_fast_kernel<8, %d, false>" % shape[2]),
+                     "kernel": kname,
                      "algorithmic_bytes_per_launch": b_slab,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"},
         "clocks": clk,
@@ -542,7 +546,9 @@ def run_ours(args, rank, world):
                 "steps": "the device-timed block steps, on a fresh solver",
                 "solver_phase_ms_per_step": e2e_phase_ms / args.steps,
                 "host_buffers": "trbl_host_alloc (cudaHostAlloc; GPU's nearest host node %d)" % numa,
-                "copy_gb_per_s": 2 * nbytes * args.steps / (copy_ms * 1e-3) / 1e9 if copy_ms > 0 else None},
+                "copy_gb_per_s": 2 * nbytes * args.steps / (copy_ms * 1e-3) / 1e9 if copy_ms > 0 else None,
+                "copy_in_ms_per_step": copy_in_ms, "copy_out_ms_per_step": copy_out_ms,
+                "other_ms_per_step": (el * 1e3 - e2e_phase_ms) / args.steps - copy_in_ms - copy_out_ms},
     }
     if rank == 0 and world == 1 and not args.no_proj:
         del sv

@@ -271,7 +271,8 @@ typedef struct trbl_params {
   int max_iter;        /* block iterations cap; 0 = 100000 */
   int check_every;     /* Rayleigh-Ritz convergence test every this many block steps (restarts always
                           test); 0 = adaptive: a test once the block steps since the previous test
-                          have taken three times as long as that test did */
+                          have taken six times as long as that test did (tests then take at most a
+                          seventh of the time) */
   uint64_t seed;       /* start block: uniform(-1,1) from splitmix64(seed<<32 + i*q + j) */
   double normH;        /* ||H|| used by tol; 0 = estimated by the solver (largest |Ritz value|) */
   int projections;     /* TRBL_PROJ_TENSOR (0, default) or TRBL_PROJ_CUDA_CORE: how the FP32
@@ -304,6 +305,8 @@ typedef struct trbl_stats {
   double ms_total, ms_apply, ms_orth, ms_qr, ms_ritz, ms_restart;
   int basis_size;      /* Lanczos vectors in the basis now (stepwise solver; the last step's for trbl_solve) */
   int second_passes;   /* block steps that ran a second full reorthogonalisation pass */
+  double ms_copy_in, ms_copy_out;  /* trbl_solver_step_host: device time of the block copies from / to
+                                      host memory (CUDA events on the solver's stream), summed */
 } trbl_stats;
 
 /* Lowest nev eigenpairs of H by the thick-restart block Lanczos method

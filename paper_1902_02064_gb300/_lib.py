@@ -46,7 +46,8 @@ class trbl_stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
                 ("status", C.c_int), ("normH", C.c_double), ("ms_total", C.c_double),
                 ("ms_apply", C.c_double), ("ms_orth", C.c_double), ("ms_qr", C.c_double),
-                ("ms_ritz", C.c_double), ("ms_restart", C.c_double), ("basis_size", C.c_int), ("second_passes", C.c_int)]
+                ("ms_ritz", C.c_double), ("ms_restart", C.c_double), ("basis_size", C.c_int), ("second_passes", C.c_int),
+                ("ms_copy_in", C.c_double), ("ms_copy_out", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -233,7 +233,7 @@ constexpr int kF2 = 80;    // pass-2 Cholesky
 constexpr int kInfo = 160; // syevd info
 constexpr int kTmaErr = 170;  // TMA wait timeout word
 constexpr int kFlagInts = 192;
-constexpr double kCheckRatio = 3.0;  // adaptive Rayleigh-Ritz cadence (see Solver::step)
+constexpr double kCheckRatio = 6.0;  // adaptive Rayleigh-Ritz cadence (see Solver::step)
 
 // ---- batched forms of a block step's small kernels ----
 // Per-set device pointers of the batched solver's step (entry s = set s).
@@ -1661,7 +1661,13 @@ struct trbl_solver {
   trbl_params params;
   cudaStream_t stream = nullptr;
   trbl::SolverBase* impl = nullptr;
-  ~trbl_solver() { delete impl; }
+  cudaEvent_t cev[4] = {nullptr, nullptr, nullptr, nullptr};  // host-buffer copies: in begin/end, out begin/end
+  double ms_copy_in = 0, ms_copy_out = 0;
+  ~trbl_solver() {
+    delete impl;
+    for (cudaEvent_t e : cev)
+      if (e) cudaEventDestroy(e);
+  }
 };
 
 using namespace trbl;
@@ -1713,33 +1719,30 @@ extern "C" int trbl_solver_step_host(trbl_solver* sv, const void* block_in, void
   clear_error();
   if (!sv || !sv->impl) return fail(TRBL_ERR_ARG, "null solver");
   const size_t bytes = sv->impl->block_bytes();
-  // with TRBL_TRACE=1, the two copies are timed with events on the stream
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  if (trace_on())
-    for (auto& e : ev) cudaEventCreate(&e);
-  if (ev[0]) cudaEventRecord(ev[0], sv->stream);
+  // the two copies are timed with events on the solver's stream
+  if (!sv->cev[0])
+    for (auto& e : sv->cev) TRBL_CUDA(cudaEventCreate(&e));
+  cudaEvent_t* ev = sv->cev;
+  TRBL_CUDA(cudaEventRecord(ev[0], sv->stream));
   if (block_in)
     TRBL_CUDA(cudaMemcpyAsync(sv->impl->block(), block_in, bytes, cudaMemcpyHostToDevice, sv->stream));
-  if (ev[1]) cudaEventRecord(ev[1], sv->stream);
+  TRBL_CUDA(cudaEventRecord(ev[1], sv->stream));
   int rc = sv->impl->step(converged);
-  if (rc == TRBL_OK && block_out) {
-    if (ev[2]) cudaEventRecord(ev[2], sv->stream);
-    rc = cudaMemcpyAsync(block_out, sv->impl->block(), bytes, cudaMemcpyDeviceToHost, sv->stream) == cudaSuccess
-             ? TRBL_OK
-             : fail(TRBL_ERR_CUDA, "cudaMemcpyAsync (block out)");
-    if (ev[3]) cudaEventRecord(ev[3], sv->stream);
-    if (rc == TRBL_OK && cudaStreamSynchronize(sv->stream) != cudaSuccess)
-      rc = fail(TRBL_ERR_CUDA, "cudaStreamSynchronize (block out)");
+  if (rc) return rc;
+  float in_ms = 0.f, out_ms = 0.f;
+  if (block_out) {
+    TRBL_CUDA(cudaEventRecord(ev[2], sv->stream));
+    TRBL_CUDA(cudaMemcpyAsync(block_out, sv->impl->block(), bytes, cudaMemcpyDeviceToHost, sv->stream));
+    TRBL_CUDA(cudaEventRecord(ev[3], sv->stream));
+    TRBL_CUDA(cudaStreamSynchronize(sv->stream));
+    TRBL_CUDA(cudaEventElapsedTime(&out_ms, ev[2], ev[3]));
   }
-  if (ev[0]) {
-    cudaStreamSynchronize(sv->stream);
-    float in_ms = 0.f, out_ms = 0.f;
-    cudaEventElapsedTime(&in_ms, ev[0], ev[1]);
-    if (block_out && rc == TRBL_OK) cudaEventElapsedTime(&out_ms, ev[2], ev[3]);
-    trace("step_host: copy in %.2f ms, copy out %.2f ms (%zu bytes each)", in_ms, out_ms, bytes);
-    for (auto& e : ev) cudaEventDestroy(e);
-  }
-  return rc;
+  TRBL_CUDA(cudaEventSynchronize(ev[1]));
+  TRBL_CUDA(cudaEventElapsedTime(&in_ms, ev[0], ev[1]));
+  if (block_in) sv->ms_copy_in += in_ms;
+  sv->ms_copy_out += out_ms;
+  trace("step_host: copy in %.2f ms, copy out %.2f ms (%zu bytes each)", in_ms, out_ms, bytes);
+  return TRBL_OK;
 }
 
 extern "C" int trbl_solver_state_bytes(trbl_solver* sv, int64_t* bytes) {
@@ -1774,6 +1777,8 @@ extern "C" int trbl_solver_stats(trbl_solver* sv, trbl_stats* st) {
   if (!sv || !sv->impl || !st) return fail(TRBL_ERR_ARG, "null argument");
   *st = trbl_stats{};
   sv->impl->stats(st);
+  st->ms_copy_in = sv->ms_copy_in;
+  st->ms_copy_out = sv->ms_copy_out;
   return TRBL_OK;
 }
 
