@@ -179,13 +179,22 @@ __global__ void __launch_bounds__(kThreadsW, 1)
       if (!w_wait(sh, &sh.accfull[a], uint32_t((j >> 1) & 1))) return false;
       tc_fence_after();
       const uint32_t ta = tmem + (uint32_t(32 * quad) << 16) + uint32_t(a * 2 * kNT + 64 * half);
+      // two rounds of four loads in flight, one wait each
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        float v[16], w[16];
-        tmem_ld16(ta + uint32_t(16 * u), v);
-        tmem_ld16(ta + uint32_t(kNT + 16 * u), w);
+      for (int h2 = 0; h2 < 2; ++h2) {
+        uint32_t v0[16], w0[16], v1[16], w1[16];
+        tmem_ld16_nowait(ta + uint32_t(32 * h2), v0);
+        tmem_ld16_nowait(ta + uint32_t(kNT + 32 * h2), w0);
+        tmem_ld16_nowait(ta + uint32_t(32 * h2 + 16), v1);
+        tmem_ld16_nowait(ta + uint32_t(kNT + 32 * h2 + 16), w1);
+        tmem_wait_ld();
 #pragma unroll
-        for (int i = 0; i < 16; ++i) sum[16 * u + i] = __fadd_rn(sum[16 * u + i], __fadd_rn(v[i], w[i]));
+        for (int i = 0; i < 16; ++i) {
+          float& s0 = sum[32 * h2 + i];
+          float& s1 = sum[32 * h2 + 16 + i];
+          s0 = __fadd_rn(s0, __fadd_rn(__uint_as_float(v0[i]), __uint_as_float(w0[i])));
+          s1 = __fadd_rn(s1, __fadd_rn(__uint_as_float(v1[i]), __uint_as_float(w1[i])));
+        }
       }
       tc_fence_before();
       __syncwarp();
@@ -197,9 +206,17 @@ __global__ void __launch_bounds__(kThreadsW, 1)
         if (r < D && c0 < n) {
           float* o = Out + r * ldo + c0;
           const int nc = std::min(64, n - c0);
+          if (nc == 64 && beta == 0.f && (reinterpret_cast<uintptr_t>(o) & 15) == 0) {
+            // 16-byte stores: a quarter of the store instructions
 #pragma unroll
-          for (int i = 0; i < 64; ++i)
-            if (i < nc) o[i] = beta != 0.f ? fmaf(beta, o[i], alpha * sum[i]) : alpha * sum[i];
+            for (int i = 0; i < 64; i += 4)
+              *reinterpret_cast<float4*>(o + i) =
+                  make_float4(alpha * sum[i], alpha * sum[i + 1], alpha * sum[i + 2], alpha * sum[i + 3]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 64; ++i)
+              if (i < nc) o[i] = beta != 0.f ? fmaf(beta, o[i], alpha * sum[i]) : alpha * sum[i];
+          }
         }
 #pragma unroll
         for (int i = 0; i < 64; ++i) sum[i] = 0.f;

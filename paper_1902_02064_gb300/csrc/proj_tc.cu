@@ -211,8 +211,12 @@ __device__ __forceinline__ void warp_arrive_async(uint64_t* bar, int lane) {
 // tensor-memory lanes a warp may read.
 __device__ __forceinline__ void acc_load2(uint32_t tmem, int warp, int a, float (&v)[16], float (&w)[16]) {
   const uint32_t base = tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(a * 2 * kN + 16 * ((warp - 2) >> 2));
-  tmem_ld16(base, v);
-  tmem_ld16(base + kN, w);
+  uint32_t rv[16], rw[16];
+  tmem_ld16_nowait(base, rv);
+  tmem_ld16_nowait(base + kN, rw);
+  tmem_wait_ld();
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(rv[i]), w[i] = __uint_as_float(rw[i]);
 }
 
 // The same, summed.
@@ -391,6 +395,18 @@ __device__ __forceinline__ void update_epilogue(TcShared& sh, uint32_t tmem, int
   if (r < D && c0 < n) {
     float* o = Out + r * ldo + c0;
     const int nc = std::min(16, n - c0);
+    if (nc == 16 && (reinterpret_cast<uintptr_t>(o) & 15) == 0) {
+      // 16-byte loads and stores
+      float4* o4 = reinterpret_cast<float4*>(o);
+      float4 old4[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) old4[k] = beta != 0.f ? o4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        o4[k] = make_float4(fmaf(beta, old4[k].x, alpha * v[4 * k]), fmaf(beta, old4[k].y, alpha * v[4 * k + 1]),
+                            fmaf(beta, old4[k].z, alpha * v[4 * k + 2]), fmaf(beta, old4[k].w, alpha * v[4 * k + 3]));
+      return;
+    }
     float old[16];
     // all loads of the row first: one memory latency per tile, not one per column
 #pragma unroll
