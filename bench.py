@@ -492,9 +492,12 @@ def run_ours(args, rank, world):
     barrier()
     se0 = sv.stats()
     t0 = time.perf_counter()
+    copy_out_steps = []
     for k in range(args.steps):
         src, dst = (host_in, host_out) if k % 2 == 0 else (host_out, host_in)
+        c0 = sv.stats()["ms_copy_out"]
         sv.step_host(src, dst)
+        copy_out_steps.append(round(sv.stats()["ms_copy_out"] - c0, 2))
     torch.cuda.synchronize()
     el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     se1 = sv.stats()
@@ -548,6 +551,7 @@ def run_ours(args, rank, world):
                 "host_buffers": "trbl_host_alloc (cudaHostAlloc; GPU's nearest host node %d)" % numa,
                 "copy_gb_per_s": 2 * nbytes * args.steps / (copy_ms * 1e-3) / 1e9 if copy_ms > 0 else None,
                 "copy_in_ms_per_step": copy_in_ms, "copy_out_ms_per_step": copy_out_ms,
+                "copy_out_ms_steps": copy_out_steps,
                 "other_ms_per_step": (el * 1e3 - e2e_phase_ms) / args.steps - copy_in_ms - copy_out_ms},
     }
     if rank == 0 and world == 1 and not args.no_proj:

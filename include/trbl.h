@@ -461,10 +461,14 @@ typedef struct trbl_solver trbl_solver;
 
 /* Page-locked host memory (cudaHostAlloc, portable) for the blocks of
  * trbl_solver_step_host, so that their copies run asynchronously at the
- * link's rate; *numa_node (may be NULL) receives the host memory node
- * nearest `device` (cudaDevAttrHostNumaId, -1 if none).  The caller owns
- * the buffer and frees it with trbl_host_free.  Errors: TRBL_ERR_ARG,
- * TRBL_ERR_OOM, TRBL_ERR_CUDA. */
+ * link's rate.  The pages are placed on the host memory node nearest
+ * `device` (cudaDevAttrHostNumaId) by binding the calling thread's NUMA
+ * policy to it during the allocation (the thread's policy is restored
+ * after; default placement where the system refuses or the device reports
+ * no node).  *numa_node (may be NULL) receives the node that holds the
+ * buffer's first page (the nearest node if that cannot be queried; -1 if
+ * neither is known).  The caller owns the buffer and frees it with
+ * trbl_host_free.  Errors: TRBL_ERR_ARG, TRBL_ERR_OOM, TRBL_ERR_CUDA. */
 int trbl_host_alloc(size_t bytes, int device, void** out, int* numa_node);
 int trbl_host_free(void* p);
 
