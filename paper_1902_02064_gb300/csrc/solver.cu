@@ -1132,10 +1132,13 @@ struct Solver {
     devinfo = flags + kInfo;
     ws.ut_bytes = rowgemm_tc_workspace_bytes(mb);
     ws.tensor = p->projections == TRBL_PROJ_TENSOR;
-    // Below K = 256 the update's per-tile epilogue dominates and the CUDA-core
-    // kernel is faster (D = 18.6M, n = 32: 2.2 vs 0.9 TB/s at K = 32, even at
-    // K = 192); the projection is faster on the tensor cores at every m.
-    ws.tc_min_k = 256;
+    // With 32 columns the tensor-core update (16-byte epilogue stores) is the
+    // faster one at every K (D = 18.6M: 2.0 against 3.2 ms at K = 32, 2.9
+    // against 4.0 ms at K = 64); with 16 columns or fewer the CUDA-core kernel
+    // stays faster below K = 256 (D = 2M, n = 16: 0.20 against 0.17 ms at
+    // K = 32, 0.78 against 0.59 ms at K = 256).  The projection is faster on
+    // the tensor cores at every m.
+    ws.tc_min_k = q >= 32 ? 1 : 256;
     trace("workspace %.3f GB at %p", ar.cap / 1e9, ar.base);
     if (cusolverDnCreate(&sol) != CUSOLVER_STATUS_SUCCESS) return fail(TRBL_ERR_CUDA, "cusolverDnCreate failed");
     TRBL_SOLVER(cusolverDnSetStream(sol, s));
