@@ -49,3 +49,29 @@ def test_host_alloc_and_free():
     with pytest.raises(trbl.TrblError) as e:
         trbl._lib._check(trbl.lib().trbl_host_free(12345))
     assert e.value.code == trbl.TRBL_ERR_ARG
+
+
+def test_copy_out_after_convergence_and_timing():
+    """Once the solver has converged a host step runs no block step: the
+    current block is copied out as it is (twice the same bytes), and the
+    copy times accumulate in the statistics."""
+    w, sa, sb, inter = synth.workload("s12_2p2n")
+    tb = trbl.Basis(sa, w.nA, sb, w.nB, w.twoM)
+    th = trbl.Hamiltonian.from_interaction(tb, inter)
+    sv = trbl.Solver(th, 4, 4, 40, 1e-8, precision=trbl.TRBL_PREC_F64, check_every=1, seed=3)
+    ptr, nbytes = sv.block()
+    bufs = [trbl.HostBuffer(nbytes, 0, dtype=np.float64) for _ in range(2)]
+    for _ in range(200):
+        if sv.step() >= 4:
+            break
+    assert sv.step() >= 4  # converged: further steps do nothing
+    st0 = sv.stats()
+    sv.step_host(None, bufs[0])
+    sv.step_host(None, bufs[1])
+    st1 = sv.stats()
+    assert st1["iterations"] == st0["iterations"]
+    assert st1["ms_copy_out"] > st0["ms_copy_out"]
+    assert np.array_equal(bufs[0].array, bufs[1].array)
+    assert np.isfinite(bufs[0].array).all() and np.abs(bufs[0].array).max() > 0
+    for b in bufs:
+        b.free()
