@@ -552,7 +552,6 @@ def run_ours(args, rank, world):
                 "copy_gb_per_s": 2 * nbytes * args.steps / (copy_ms * 1e-3) / 1e9 if copy_ms > 0 else None,
                 "copy_in_ms_per_step": copy_in_ms, "copy_out_ms_per_step": copy_out_ms,
                 "copy_out_ms_steps": copy_out_steps,
-                "copy_out": "starts after the block QR and overlaps the step's Rayleigh-Ritz test and append/restart",
                 "ms_beyond_solver_phases_per_step": (el * 1e3 - e2e_phase_ms) / args.steps},
     }
     if rank == 0 and world == 1 and not args.no_proj:

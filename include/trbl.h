@@ -306,8 +306,7 @@ typedef struct trbl_stats {
   int basis_size;      /* Lanczos vectors in the basis now (stepwise solver; the last step's for trbl_solve) */
   int second_passes;   /* block steps that ran a second full reorthogonalisation pass */
   double ms_copy_in, ms_copy_out;  /* trbl_solver_step_host: device time of the block copies from / to
-                                      host memory (CUDA events), summed; the copy out overlaps the
-                                      step's tail */
+                                      host memory (CUDA events on the solver's stream), summed */
 } trbl_stats;
 
 /* Lowest nev eigenpairs of H by the thick-restart block Lanczos method
@@ -420,11 +419,9 @@ int trbl_apply_set_compensated(trbl_hamiltonian* h, int on);
  * trbl_solver_step_host: the same step with the current block V_k read from
  *   host memory block_in (D x q, row-major, element type of the precision:
  *   FP64 or FP32; NULL keeps the device copy) before the step and the next
- *   block written to host memory block_out (same layout; NULL skips); the
- *   copy out starts as soon as the block QR has formed V_{k+1}, on a stream
- *   of the solver's own, beside the step's Rayleigh-Ritz test and append or
- *   restart, and has finished when the call returns.  Pinned host memory
- *   (trbl_host_alloc) makes the copies asynchronous.
+ *   block written to host memory block_out (same layout; NULL skips) after
+ *   it.  Pinned host memory (trbl_host_alloc) makes the copies
+ *   asynchronous.
  * trbl_solver_block: device address and byte size of the current block V_k
  *   (D x q row-major), valid until the next step.
  * trbl_solver_stats: statistics so far (ms_total counts from creation).

@@ -499,12 +499,6 @@ struct Solver {
   bool skip_warmup = false;  // batch members after the first share the warmed eigensolver
 
   ~Solver() {
-    if (copy_s) {
-      cudaStreamSynchronize(copy_s);
-      cudaStreamDestroy(copy_s);
-    }
-    for (cudaEvent_t e : copy_ev)
-      if (e) cudaEventDestroy(e);
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     if (sol) cusolverDnDestroy(sol);
@@ -734,16 +728,6 @@ struct Solver {
     return TRBL_OK;
   }
 
-  // ---- host copy of the new block, overlapped with the step's tail ----
-  // Set by trbl_solver_step_host for one step: once the block QR has
-  // written V_{k+1} (nothing later in the step writes it), the copy to host
-  // memory starts on copy_s and runs beside the Rayleigh-Ritz test and the
-  // append or restart; the step returns after both have finished.
-  void* copy_out = nullptr;
-  cudaStream_t copy_s = nullptr;
-  cudaEvent_t copy_ev[3] = {nullptr, nullptr, nullptr};  // QR done, copy start, copy end
-  float copy_out_ms = 0.f;
-
   // ---- stepping state ----
   Timer tm;
   cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -795,13 +779,6 @@ struct Solver {
     tm.rec(2, s);
     TRY(block_qr(nb));
     tm.rec(3, s);
-    if (copy_out) {
-      TRBL_CUDA(cudaEventRecord(copy_ev[0], s));
-      TRBL_CUDA(cudaStreamWaitEvent(copy_s, copy_ev[0], 0));
-      TRBL_CUDA(cudaEventRecord(copy_ev[1], copy_s));
-      TRBL_CUDA(cudaMemcpyAsync(copy_out, Vk, sizeof(T) * size_t(D) * q, cudaMemcpyDeviceToHost, copy_s));
-      TRBL_CUDA(cudaEventRecord(copy_ev[2], copy_s));
-    }
     ++iter;
     const bool need_restart = nb + q > mb;
     // Rayleigh-Ritz cadence: every check_every steps, or (check_every = 0)
@@ -843,11 +820,6 @@ struct Solver {
     }
     tm.rec(5, s);
     TRBL_CUDA(cudaEventSynchronize(tm.ev[5]));
-    if (copy_out) {
-      TRBL_CUDA(cudaEventSynchronize(copy_ev[2]));
-      TRBL_CUDA(cudaEventElapsedTime(&copy_out_ms, copy_ev[1], copy_ev[2]));
-      copy_out = nullptr;
-    }
     ms_apply += tm.ms(0, 1);
     ms_orth += tm.ms(1, 2);
     ms_qr += tm.ms(2, 3);
@@ -1214,9 +1186,6 @@ struct SolverBase {
   virtual size_t state_bytes() = 0;
   virtual int save(void* host, int64_t bytes) = 0;
   virtual int load(const void* host, int64_t bytes) = 0;
-  // The next step() copies its new block to host (see Solver::copy_out);
-  // returns the copy's device time in ms through *ms after that step.
-  virtual int step_copy_out(void* host, int* conv, float* ms) = 0;
 };
 
 template <typename T>
@@ -1224,33 +1193,6 @@ struct SolverImpl : SolverBase {
   Solver<T> S{};
   int init() override { return S.init(); }
   int step(int* c) override { return S.step(c); }
-  int step_copy_out(void* host, int* c, float* ms) override {
-    if (!S.copy_s) {
-      TRBL_CUDA(cudaStreamCreateWithFlags(&S.copy_s, cudaStreamNonBlocking));
-      for (auto& e : S.copy_ev) TRBL_CUDA(cudaEventCreate(&e));
-    }
-    if (S.done) {
-      // no step runs: the block is copied as it is
-      *ms = 0.f;
-      TRBL_CUDA(cudaEventRecord(S.copy_ev[1], S.s));
-      TRBL_CUDA(cudaMemcpyAsync(host, S.Vk, block_bytes(), cudaMemcpyDeviceToHost, S.s));
-      TRBL_CUDA(cudaEventRecord(S.copy_ev[2], S.s));
-      TRBL_CUDA(cudaEventSynchronize(S.copy_ev[2]));
-      TRBL_CUDA(cudaEventElapsedTime(ms, S.copy_ev[1], S.copy_ev[2]));
-      if (c) *c = S.conv;
-      return TRBL_OK;
-    }
-    S.copy_out = host;
-    S.copy_out_ms = 0.f;
-    const int rc = S.step(c);
-    if (S.copy_out) {
-      // the step stopped early with an error: let a copy it may have started finish
-      S.copy_out = nullptr;
-      cudaStreamSynchronize(S.copy_s);
-    }
-    *ms = S.copy_out_ms;
-    return rc;
-  }
   int finish(double* e, double* r, void* v, trbl_stats* st) override { return S.finish(e, r, v, st); }
   void stats(trbl_stats* st) override {
     S.fill_stats(st, TRBL_OK);
@@ -1780,9 +1722,7 @@ extern "C" int trbl_solver_step_host(trbl_solver* sv, const void* block_in, void
   clear_error();
   if (!sv || !sv->impl) return fail(TRBL_ERR_ARG, "null solver");
   const size_t bytes = sv->impl->block_bytes();
-  // the copy in is timed with events on the solver's stream; the copy out
-  // starts right after the block QR, on a stream of its own, and overlaps
-  // the rest of the step
+  // the two copies are timed with events on the solver's stream
   if (!sv->cev[0])
     for (auto& e : sv->cev) TRBL_CUDA(cudaEventCreate(&e));
   cudaEvent_t* ev = sv->cev;
@@ -1790,9 +1730,16 @@ extern "C" int trbl_solver_step_host(trbl_solver* sv, const void* block_in, void
   if (block_in)
     TRBL_CUDA(cudaMemcpyAsync(sv->impl->block(), block_in, bytes, cudaMemcpyHostToDevice, sv->stream));
   TRBL_CUDA(cudaEventRecord(ev[1], sv->stream));
-  float in_ms = 0.f, out_ms = 0.f;
-  const int rc = block_out ? sv->impl->step_copy_out(block_out, converged, &out_ms) : sv->impl->step(converged);
+  int rc = sv->impl->step(converged);
   if (rc) return rc;
+  float in_ms = 0.f, out_ms = 0.f;
+  if (block_out) {
+    TRBL_CUDA(cudaEventRecord(ev[2], sv->stream));
+    TRBL_CUDA(cudaMemcpyAsync(block_out, sv->impl->block(), bytes, cudaMemcpyDeviceToHost, sv->stream));
+    TRBL_CUDA(cudaEventRecord(ev[3], sv->stream));
+    TRBL_CUDA(cudaStreamSynchronize(sv->stream));
+    TRBL_CUDA(cudaEventElapsedTime(&out_ms, ev[2], ev[3]));
+  }
   TRBL_CUDA(cudaEventSynchronize(ev[1]));
   TRBL_CUDA(cudaEventElapsedTime(&in_ms, ev[0], ev[1]));
   if (block_in) sv->ms_copy_in += in_ms;
