@@ -271,8 +271,8 @@ typedef struct trbl_params {
   int max_iter;        /* block iterations cap; 0 = 100000 */
   int check_every;     /* Rayleigh-Ritz convergence test every this many block steps (restarts always
                           test); 0 = adaptive: a test once the block steps since the previous test
-                          have taken six times as long as that test did (tests then take at most a
-                          seventh of the time) */
+                          have taken twelve times as long as that test did (tests then take at most
+                          a thirteenth of the time) */
   uint64_t seed;       /* start block: uniform(-1,1) from splitmix64(seed<<32 + i*q + j) */
   double normH;        /* ||H|| used by tol; 0 = estimated by the solver (largest |Ritz value|) */
   int projections;     /* TRBL_PROJ_TENSOR (0, default) or TRBL_PROJ_CUDA_CORE: how the FP32

@@ -233,7 +233,7 @@ constexpr int kF2 = 80;    // pass-2 Cholesky
 constexpr int kInfo = 160; // syevd info
 constexpr int kTmaErr = 170;  // TMA wait timeout word
 constexpr int kFlagInts = 192;
-constexpr double kCheckRatio = 6.0;  // adaptive Rayleigh-Ritz cadence (see Solver::step)
+constexpr double kCheckRatio = 12.0;  // adaptive Rayleigh-Ritz cadence (see Solver::step)
 
 // ---- batched forms of a block step's small kernels ----
 // Per-set device pointers of the batched solver's step (entry s = set s).
