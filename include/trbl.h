@@ -278,6 +278,12 @@ typedef struct trbl_params {
   int projections;     /* TRBL_PROJ_TENSOR (0, default) or TRBL_PROJ_CUDA_CORE: how the FP32
                           projections and updates of mixed precision are computed */
   int reorth;          /* TRBL_REORTH_SELECTIVE (0, default) or TRBL_REORTH_TWICE (below) */
+  int refine;          /* trbl_solve in TRBL_PREC_MIXED: 1 = when the true residuals (FP64 apply)
+                          of the converged pairs exceed tol * ||H||, lower the estimate's target
+                          (below tol by the measured gap) and iterate on, at most three rounds,
+                          until they meet tol or the FP32 floor alone reaches 0.9 tol; 0 = stop
+                          at the estimate (default).  Ignored by the stepwise and batched
+                          solvers. */
 } trbl_params;
 
 /* Reorthogonalisation of a block step (Sec. III C/D: the block is made
@@ -287,9 +293,8 @@ typedef struct trbl_params {
  *   components), one full pass against every stored vector, and a second
  *   full pass only in the steps where a column of the block lost more than
  *   half its squared norm in the first (the Daniel-Gragg-Kaufman-Stewart
- *   test; after a thick restart the couplings to the kept Ritz vectors make
- *   the test fire).  One full pass removes what the first leaves when the
- *   block was already orthogonal to the basis up to rounding.
+ *   test).  One full pass removes what the first leaves when the block was
+ *   already orthogonal to the basis up to rounding.
  * TRBL_REORTH_TWICE: two full passes every step (classical Gram-Schmidt
  *   applied twice). */
 #define TRBL_REORTH_SELECTIVE 0

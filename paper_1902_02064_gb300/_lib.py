@@ -39,7 +39,7 @@ class trbl_params(C.Structure):
     _fields_ = [("nev", C.c_int), ("q", C.c_int), ("max_basis", C.c_int), ("keep", C.c_int),
                 ("tol", C.c_double), ("precision", C.c_int), ("max_iter", C.c_int),
                 ("check_every", C.c_int), ("seed", C.c_uint64), ("normH", C.c_double),
-                ("projections", C.c_int), ("reorth", C.c_int)]
+                ("projections", C.c_int), ("reorth", C.c_int), ("refine", C.c_int)]
 
 
 class trbl_stats(C.Structure):
@@ -349,11 +349,13 @@ def solve(h: Hamiltonian, nev: int, q: int, max_basis: int, tol: float,
           precision: int = TRBL_PREC_F64, keep: int = 0, max_iter: int = 0,
           check_every: int = 0, seed: int = 1, normH: float = 0.0, want_vectors: bool = True,
           stream=None, raise_on_noconv: bool = True, projections: int = TRBL_PROJ_TENSOR,
-          reorth: int = TRBL_REORTH_SELECTIVE):
-    """Lowest nev eigenpairs by trbl_solve.  Returns (evals, resid, evecs or None, stats dict)."""
+          reorth: int = TRBL_REORTH_SELECTIVE, refine: bool = False):
+    """Lowest nev eigenpairs by trbl_solve.  Returns (evals, resid, evecs or None, stats dict).
+    refine (mixed precision): iterate on until the true residuals meet tol."""
     import torch
     D = h.basis.dim
-    p = _params(nev, q, max_basis, tol, precision, keep, max_iter, check_every, seed, normH, projections, reorth)
+    p = _params(nev, q, max_basis, tol, precision, keep, max_iter, check_every, seed, normH, projections, reorth,
+                refine)
     st = trbl_stats()
     ev = np.zeros(nev)
     rs = np.zeros(nev)
@@ -372,9 +374,10 @@ def solve(h: Hamiltonian, nev: int, q: int, max_basis: int, tol: float,
 
 
 def _params(nev, q, max_basis, tol, precision=TRBL_PREC_F64, keep=0, max_iter=0, check_every=0, seed=1,
-            normH=0.0, projections=TRBL_PROJ_TENSOR, reorth=TRBL_REORTH_SELECTIVE):
+            normH=0.0, projections=TRBL_PROJ_TENSOR, reorth=TRBL_REORTH_SELECTIVE, refine=False):
     return trbl_params(int(nev), int(q), int(max_basis), int(keep), float(tol), int(precision),
-                       int(max_iter), int(check_every), int(seed), float(normH), int(projections), int(reorth))
+                       int(max_iter), int(check_every), int(seed), float(normH), int(projections), int(reorth),
+                       int(bool(refine)))
 
 
 def trbl_solver_create(h: int, params: trbl_params, stream: int = 0) -> int:

@@ -728,6 +728,10 @@ struct Solver {
     return TRBL_OK;
   }
 
+  // target of the residual estimate as a fraction of tol (trbl_solve's
+  // refinement lowers it when the true residuals of mixed precision miss tol)
+  double est_scale = 1.0;
+
   // ---- stepping state ----
   Timer tm;
   cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -790,7 +794,7 @@ struct Solver {
     if (check) {
       TRY(ritz(nb));
       have_ritz = true;
-      const double lim = p->tol * normH;
+      const double lim = p->tol * normH * est_scale;
       conv = 0;
       for (int i = 0; i < std::min(nev, nb); ++i)
         if (hbuf[mb + i] <= lim) ++conv;
@@ -865,7 +869,7 @@ struct Solver {
     const bool check = !appended || check_due || iter >= max_iter;
     if (check && !done) {
       TRY(ritz(nb_old));
-      const double lim = p->tol * normH;
+      const double lim = p->tol * normH * est_scale;
       conv = 0;
       for (int i = 0; i < std::min(nev, nb_old); ++i)
         if (hbuf[mb + i] <= lim) ++conv;
@@ -1186,6 +1190,9 @@ struct SolverBase {
   virtual size_t state_bytes() = 0;
   virtual int save(void* host, int64_t bytes) = 0;
   virtual int load(const void* host, int64_t bytes) = 0;
+  // Lower the estimate's target to scale * tol and let the solver step on.
+  virtual void retarget(double scale) = 0;
+  virtual double norm_h() = 0;
 };
 
 template <typename T>
@@ -1205,6 +1212,12 @@ struct SolverImpl : SolverBase {
   void* block() override { return S.Vk; }
   size_t block_bytes() override { return sizeof(T) * size_t(S.D) * S.q; }
   bool is_done() override { return S.done; }
+  void retarget(double scale) override {
+    S.est_scale = scale;
+    S.done = false;
+    S.finished = false;
+  }
+  double norm_h() override { return S.normH; }
   int iterations() override { return S.iter; }
   size_t state_bytes() override { return S.state_bytes(); }
   int save(void* host, int64_t bytes) override { return S.save(host, bytes); }
@@ -1814,7 +1827,40 @@ extern "C" int trbl_solve(const trbl_hamiltonian* h, const trbl_params* p, doubl
   }
   const int max_iter = p->max_iter > 0 ? p->max_iter : 100000;
   while (rc == TRBL_OK && !sv->impl->is_done() && sv->impl->iterations() < max_iter) rc = sv->impl->step(nullptr);
-  if (rc == TRBL_OK) rc = trbl_solver_finish(sv, evals, resid, evecs, stats);
+  const bool refine = p->refine && p->precision == TRBL_PREC_MIXED;
+  std::vector<double> rloc;
+  double* rr = resid;
+  if (refine && !rr) {
+    rloc.assign(size_t(p->nev), 0.0);
+    rr = rloc.data();
+  }
+  if (rc == TRBL_OK) rc = trbl_solver_finish(sv, evals, rr, evecs, stats);
+  // Refinement: the estimate bounds the residual of the FP32 Lanczos
+  // recurrence; the FP32 vectors and product add a floor of their own, so a
+  // true residual may exceed tol when the estimate meets it.  Taking the
+  // floor as the measured gap (true^2 - estimate^2), lower the estimate's
+  // target so that both together stay below 0.9 tol, and step on; stop when
+  // the true residuals meet tol, the floor alone reaches 0.9 tol, or after
+  // three rounds.
+  double scale = 1.0;
+  for (int round = 0; refine && rc == TRBL_OK && round < 3; ++round) {
+    const double lim = p->tol * sv->impl->norm_h();
+    double worst = 0.0;
+    for (int i = 0; i < p->nev; ++i)
+      if (std::isfinite(rr[i])) worst = std::max(worst, rr[i]);
+    if (worst <= lim || sv->impl->iterations() >= max_iter) break;
+    const double est = lim * scale, target = 0.9 * lim;
+    const double floor2 = std::max(0.0, worst * worst - est * est);
+    if (floor2 >= target * target) break;
+    double next = std::sqrt(target * target - floor2) / lim;
+    if (!(next < scale)) next = 0.8 * scale;
+    scale = next;
+    trace("refine round %d: worst true residual %.3g of tol %.3g, estimate target %.3f tol", round, worst / lim * p->tol,
+          p->tol, scale);
+    sv->impl->retarget(scale);
+    while (rc == TRBL_OK && !sv->impl->is_done() && sv->impl->iterations() < max_iter) rc = sv->impl->step(nullptr);
+    if (rc == TRBL_OK) rc = trbl_solver_finish(sv, evals, rr, evecs, stats);
+  }
   std::string keep = trbl_last_error();
   trbl_solver_destroy(sv);
   if (rc != TRBL_OK) fail(rc, "%s", keep.c_str());

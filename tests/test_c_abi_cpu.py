@@ -91,3 +91,53 @@ def test_c_program_drives_the_host_entry_points(tmp_path):
     assert out[1] == "pf 1963461"
     assert out[2].startswith("null %d " % trbl.TRBL_ERR_ARG)
     assert out[3].startswith("nan %d " % trbl.TRBL_ERR_ARG) and "h1A[0] is not finite" in out[3]
+
+
+LAYOUT = r"""
+#include "trbl.h"
+#include <stddef.h>
+#include <stdio.h>
+#define F(S, m) printf(#S " " #m " %zu %zu\n", offsetof(S, m), sizeof(((S*)0)->m))
+int main(void) {
+  printf("trbl_params size %zu\n", sizeof(trbl_params));
+  F(trbl_params, nev); F(trbl_params, q); F(trbl_params, max_basis); F(trbl_params, keep);
+  F(trbl_params, tol); F(trbl_params, precision); F(trbl_params, max_iter); F(trbl_params, check_every);
+  F(trbl_params, seed); F(trbl_params, normH); F(trbl_params, projections); F(trbl_params, reorth);
+  F(trbl_params, refine);
+  printf("trbl_stats size %zu\n", sizeof(trbl_stats));
+  F(trbl_stats, iterations); F(trbl_stats, restarts); F(trbl_stats, converged); F(trbl_stats, status);
+  F(trbl_stats, normH); F(trbl_stats, ms_total); F(trbl_stats, ms_apply); F(trbl_stats, ms_orth);
+  F(trbl_stats, ms_qr); F(trbl_stats, ms_ritz); F(trbl_stats, ms_restart); F(trbl_stats, basis_size);
+  F(trbl_stats, second_passes); F(trbl_stats, ms_copy_in); F(trbl_stats, ms_copy_out);
+  return 0;
+}
+"""
+
+
+def test_struct_layouts_match_the_python_binding(tmp_path):
+    """trbl_params and trbl_stats as the C compiler lays them out (offset and
+    size of every member, whole size) equal the ctypes structures the Python
+    binding passes through the ABI."""
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not found")
+    import ctypes
+    from paper_1902_02064_gb300 import _lib
+    src = tmp_path / "layout.c"
+    src.write_text(LAYOUT)
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-o", str(exe)], check=True, capture_output=True, text=True)
+    lines = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = {"trbl_params": set(), "trbl_stats": set()}
+    for ln in lines:
+        parts = ln.split()
+        if len(parts) == 3 and parts[1] == "size":
+            assert int(parts[2]) == ctypes.sizeof(getattr(_lib, parts[0])), ln
+        elif len(parts) == 4:
+            cls = getattr(_lib, parts[0])
+            fld = getattr(cls, parts[1])
+            assert (fld.offset, fld.size) == (int(parts[2]), int(parts[3])), ln
+            seen[parts[0]].add(parts[1])
+    for name, got in seen.items():
+        assert got == {f for f, _ in getattr(_lib, name)._fields_}, name

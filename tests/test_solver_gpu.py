@@ -173,3 +173,25 @@ def test_selective_and_twice_reorthogonalisation_agree(medium, precision, tol, b
     assert res[trbl.TRBL_REORTH_TWICE]["second_passes"] == 0  # counted for the selective schedule only
     with pytest.raises(trbl.TrblError):
         trbl.solve(th, w.nev, w.q, w.max_basis, tol, precision=precision, reorth=7)
+
+
+@pytest.mark.parametrize("tol", [3e-7, 1.5e-7])
+def test_mixed_refinement_of_true_residuals(medium, tol):
+    """refine=True (mixed precision): when the true residuals of the pairs
+    whose estimates met tol exceed tol ||H||, the solve lowers the estimate's
+    target and iterates on.  With refinement the worst true residual meets tol
+    or, where the FP32 floor does not allow that, is no larger than without;
+    the eigenvalues stay within the mixed bar of the oracle's."""
+    w, gold, th = medium
+    normH = gold["normH"]
+    ref = np.array(gold["evals"][: w.nev])
+    kw = dict(precision=trbl.TRBL_PREC_MIXED, want_vectors=False, raise_on_noconv=False, max_iter=20000)
+    e0, r0, _, s0 = trbl.solve(th, w.nev, w.q, w.max_basis, tol, **kw)
+    e1, r1, _, s1 = trbl.solve(th, w.nev, w.q, w.max_basis, tol, refine=True, **kw)
+    assert s1["iterations"] >= s0["iterations"]
+    lim = tol * s1["normH"]
+    if r0.max() > tol * s0["normH"]:
+        assert r1.max() <= lim or r1.max() <= r0.max(), (r0.max() / s0["normH"], r1.max() / s1["normH"])
+    else:
+        assert s1["iterations"] == s0["iterations"]
+    assert np.abs(e1 - ref).max() <= 1e-6 * normH
