@@ -79,9 +79,11 @@ __global__ void __launch_bounds__(NP * 16) rowgemm_tma_kernel(const __grid_const
   const int row8 = lane >> 2, cq = lane & 3;
   const int rbase = rb * 32 + row8;  // rows rbase + 8 i
   const int cbase = ch * 16 + cq * 4;
-  float acc[4][4];
+  // acc sums one 32-wide K chunk; tot sums the chunks (round-to-nearest
+  // adds), so a long K does not run through one FP32 accumulator
+  float acc[4][4], tot[4][4];
   for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < 4; ++j) acc[i][j] = tot[i][j] = 0.f;
   int64_t j = 0;
   for (; j < njobs; ++j) {
     const int s = int(j % nstage);
@@ -99,6 +101,11 @@ __global__ void __launch_bounds__(NP * 16) rowgemm_tma_kernel(const __grid_const
       for (int i = 0; i < 4; ++i)
         for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fmaf(b[i], u[jj], acc[i][jj]);
     }
+    for (int i = 0; i < 4; ++i)
+      for (int jj = 0; jj < 4; ++jj) {
+        tot[i][jj] = __fadd_rn(tot[i][jj], acc[i][jj]);
+        acc[i][jj] = 0.f;
+      }
     if (kc == nk - 1) {
       const int64_t ti = blockIdx.x + (j / nk) * gridDim.x;
       for (int i = 0; i < 4; ++i) {
@@ -108,12 +115,12 @@ __global__ void __launch_bounds__(NP * 16) rowgemm_tma_kernel(const __grid_const
             const int c = cbase + jj;
             if (c < n) {
               float* o = Out + r * ldo + c;
-              const float v = alpha * acc[i][jj];
+              const float v = alpha * tot[i][jj];
               *o = (beta == 0.f) ? v : fmaf(beta, *o, v);
             }
           }
         }
-        for (int jj = 0; jj < 4; ++jj) acc[i][jj] = 0.f;
+        for (int jj = 0; jj < 4; ++jj) tot[i][jj] = 0.f;
       }
     }
     __syncthreads();  // stage s fully read
