@@ -175,6 +175,25 @@ def measured_peaks():
         return None
 
 
+def product_kernel_name(shape, q):
+    """The kernel(s) of one block product for a launch shape (kernel, rows per
+    work item, blocks per SM) at FP32 rows of q values: the split product is
+    two launches, the like-particle grouped kernel then the cross-term
+    kernel."""
+    kern, rows, bps = shape
+    grouped = "apply_grouped_kernel<float, %d, %d>" % {8: (2, 1), 16: (4, 1), 32: (8, 1)}.get(q, (4, 4))
+    if kern == 5:
+        return "%s + apply_pn_tma_kernel" % grouped
+    if kern in (3, 4):
+        v = (4, 4, 512, 2) if kern == 4 else ((8, 4, 512, 1) if bps == 1 else (8, 2, 384, 2))
+        return "%s + apply_pn_kernel<%d, %d, %d, %d>" % ((grouped,) + v)
+    if kern == 2:
+        return "apply_grouped_kernel<float, %d, 2>" % {8: 1, 16: 2, 32: 4}.get(q, 4)
+    if kern == 1:
+        return "apply_fast_kernel<%d, %d, false>" % ({8: 2, 16: 4}.get(q, 8), bps)
+    return grouped
+
+
 def ncu_traffic(kernel, rows_per_item, path=os.path.join(ROOT, "profiles", "apply_traffic.json")):
     """(DRAM bytes per apply launch, kernel name) from a committed ncu summary.
     The bytes are None unless the summary was taken on the same kernel, on its
@@ -184,13 +203,21 @@ def ncu_traffic(kernel, rows_per_item, path=os.path.join(ROOT, "profiles", "appl
         d = json.load(open(path))
     except (OSError, ValueError):
         return None, None
-    name = "apply_fast.cu" if kernel.startswith("apply_fast") else "apply_grouped.cu"
-    src = os.path.join(ROOT, "paper_1902_02064_gb300", "csrc", name)
-    try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    except OSError:
-        sha = None
-    if d.get("kernel") != kernel or d.get("source_sha256") != sha or d.get("rows_per_item", 128) != rows_per_item:
+    if "apply_pn" in kernel:
+        names = ["apply_grouped.cu", "apply_pn.cu"]
+    else:
+        names = ["apply_fast.cu" if kernel.startswith("apply_fast") else "apply_grouped.cu"]
+    shas = {}
+    for name in names:
+        try:
+            shas[name] = hashlib.sha256(open(os.path.join(ROOT, "paper_1902_02064_gb300", "csrc", name),
+                                             "rb").read()).hexdigest()
+        except OSError:
+            shas[name] = None
+    stored = d.get("source_sha256")
+    if not isinstance(stored, dict):
+        stored = {names[0]: stored}
+    if d.get("kernel") != kernel or stored != shas or d.get("rows_per_item", 128) != rows_per_item:
         return None, d.get("kernel")
     return d.get("dram_bytes_per_launch_full_size"), d.get("kernel")
 
@@ -470,8 +497,7 @@ def run_ours(args, rank, world):
     value = job_throughput(nnz * q * args.steps, ms * 1e-3, world) / 1e9
     ms_apply = (st1["ms_apply"] - st0["ms_apply"]) / args.steps
     achieved = b_slab / (ms_apply * 1e-3) / 1e9
-    kname = {0: "apply_grouped_kernel<float, 8, 1>", 2: "apply_grouped_kernel<float, 4, 2>"}.get(
-        shape[0], "apply_fast_kernel<8, %d, false>" % shape[2])
+    kname = product_kernel_name(shape, q)
     traffic, _ = ncu_traffic(kname, tune_rows)
 
     # end to end: the same block steps as the device-timed region (a fresh
@@ -531,8 +557,10 @@ def run_ours(args, rank, world):
                   "share_of_step": ms_apply / ms_step,
                   "autotune": {"shapes": "(kernel, rows per item, blocks per SM): grouped 16/32/64/128 at 8; "
                                          "fast 16/32/64 at 8; fast 16/32/64 at 6; grouped with two 16-byte "
-                                         "chunks per lane 16/32/64 at 8",
-                               "ms": tune_ms, "chosen": {"kernel": ["grouped", "fast", "grouped_x2"][shape[0]],
+                                         "chunks per lane 16/32/64 at 8; split 64 at 2; split with four "
+                                         "jumps per batch 64 at 2",
+                               "ms": tune_ms, "chosen": {"kernel": ["grouped", "fast", "grouped_x2", "split",
+                                                                    "split_x4"][shape[0]],
                                                          "rows_per_item": shape[1], "blocks_per_sm": shape[2]}}},
         "phases_ms_per_step": {k: (st1[k] - st0[k]) / args.steps
                                for k in ("ms_apply", "ms_orth", "ms_qr", "ms_ritz", "ms_restart")},
@@ -666,7 +694,7 @@ def time_to_nev_large(trbl, name, arms, th=None):
     shape = trbl.apply_get_shape(th)
     torch.cuda.empty_cache()
     out = {"workload": name, "dim": th.basis.dim, "nev": w.nev, "max_basis": w.max_basis, "tol_rel_normH": 1e-6,
-           "product_shape": {"kernel": ["grouped", "fast", "grouped_x2"][shape[0]], "rows_per_item": shape[1],
+           "product_shape": {"kernel": ["grouped", "fast", "grouped_x2", "split", "split_x4", "split_tma"][shape[0]], "rows_per_item": shape[1],
                              "blocks_per_sm": shape[2]}}
     first = None
     for label, prec, q in arms:
@@ -818,7 +846,8 @@ def run_apply_only(args):
     if args.rows:
         tune_ms, tune_rows = None, args.rows
         kern = {"grouped": trbl.TRBL_APPLY_GROUPED, "fast": trbl.TRBL_APPLY_FAST,
-                "grouped_x2": trbl.TRBL_APPLY_GROUPED_X2}[args.kernel]
+                "grouped_x2": trbl.TRBL_APPLY_GROUPED_X2, "split": trbl.TRBL_APPLY_SPLIT,
+                "split_x4": trbl.TRBL_APPLY_SPLIT_X4, "split_tma": trbl.TRBL_APPLY_SPLIT_TMA}[args.kernel]
         trbl.apply_set_shape(th, kern, args.rows, args.bps)
         trbl.apply_set_compensated(th, args.comp)
     else:
@@ -877,9 +906,9 @@ def main():
     ap.add_argument("--q", type=int, default=0)
     ap.add_argument("--rows", type=int, default=0,
                     help="--apply-only: fixed neutron rows per work item instead of the autotuner's choice")
-    ap.add_argument("--kernel", default="fast", choices=["fast", "grouped", "grouped_x2"],
+    ap.add_argument("--kernel", default="fast", choices=["fast", "grouped", "grouped_x2", "split", "split_x4", "split_tma"],
                     help="--apply-only with --rows: the product kernel")
-    ap.add_argument("--bps", type=int, default=8, choices=[6, 8],
+    ap.add_argument("--bps", type=int, default=8, choices=[1, 2, 6, 8],
                     help="--apply-only with --rows: resident blocks per SM of the fast kernel")
     ap.add_argument("--comp", action="store_true",
                     help="--apply-only with --rows: compensated row sums in the fast kernel")

@@ -370,13 +370,38 @@ int trbl_solve_batch(const trbl_hamiltonian* const* hs, int nset, const trbl_par
  * moving two 16-byte chunks of the V row (rows of 32, 64 or 128 bytes;
  * other rows as TRBL_APPLY_GROUPED). */
 #define TRBL_APPLY_GROUPED_X2 2
+/* Split product for FP32 and q a multiple of 16 (16-byte aligned rows,
+ * D * ld < 2^31): the like-particle terms (App. B.1) by the grouped kernel,
+ * then the factorised proton-neutron term (App. B.2, Eq. (pntwobodybit)) by
+ * a source-stationary kernel.  That kernel owns a 16-column slice of one
+ * target slab (a proton determinant's neutron rows) in shared memory; each
+ * source row V[p, n, :] it gathers is multiplied into every outgoing neutron
+ * jump of n at once, so a row is read once per transfer class instead of
+ * once per generated element.  Its sums are formed with shared-memory
+ * atomic adds, so the FP32 rounding of W can differ from run to run (within
+ * the same error bound); the other kernels are deterministic.  Other
+ * products run as TRBL_APPLY_GROUPED.  Blocks per SM of the cross-term
+ * kernel: 2 (384 threads, 8 outgoing jumps per register batch, two row
+ * gathers in flight per lane group) or 1 (512 threads, 8 jumps, four
+ * gathers in flight). */
+#define TRBL_APPLY_SPLIT 3
+/* The split product with 4 outgoing jumps per register batch and four row
+ * gathers in flight per lane group, 2 blocks of 512 threads per SM. */
+#define TRBL_APPLY_SPLIT_X4 4
+/* The split product whose cross-term kernel stages the source rows in
+ * shared memory by TMA (chunks of consecutive source rows, one 16-column x
+ * 32-row box per proton jump, two chunks in flight) and runs one source
+ * row per warp, its 8 lane groups on 8 outgoing jumps; 1 block per SM. */
+#define TRBL_APPLY_SPLIT_TMA 5
 /* Launch shapes trbl_apply_autotune times, in this order (kernel, neutron
  * rows per work item, resident blocks per SM): grouped 16/32/64/128; fast
  * 16/32/64 at 8 blocks per SM (32 registers a thread); fast 16/32/64 at 6
- * blocks per SM (40 registers); grouped with two chunks per lane 16/32/64.
+ * blocks per SM (40 registers); grouped with two chunks per lane 16/32/64;
+ * split at 64 rows (rows per work item of its like-particle launch) at 2
+ * blocks per SM and split with four jumps per batch at 64 rows.
  * Lanes per element and chunks per lane follow from the kernel and the row
  * width (one lane group reads one whole V row). */
-#define TRBL_TUNE_CANDIDATES 13
+#define TRBL_TUNE_CANDIDATES 15
 
 /* Times the block product of h at block size q and dtype for each launch
  * shape above that applies and keeps the fastest; ms [TRBL_TUNE_CANDIDATES]
@@ -391,9 +416,12 @@ int trbl_apply_autotune(trbl_hamiltonian* h, int q, int dtype, float* ms, int* b
  * a product of h is running.  Errors: TRBL_ERR_ARG. */
 int trbl_apply_set_rows(trbl_hamiltonian* h, int rows_per_item);
 
-/* Sets the whole launch shape: kernel (TRBL_APPLY_GROUPED, TRBL_APPLY_FAST
- * or TRBL_APPLY_GROUPED_X2), rows per work item (1..4096) and resident blocks per SM
- * of the fast kernel (6 or 8).  Same rules as trbl_apply_set_rows.  Errors:
+/* Sets the whole launch shape: kernel (TRBL_APPLY_GROUPED, TRBL_APPLY_FAST,
+ * TRBL_APPLY_GROUPED_X2, TRBL_APPLY_SPLIT or TRBL_APPLY_SPLIT_X4), rows per
+ * work item (1..4096) and resident blocks per SM (6 or 8 for the fast
+ * kernel, 1 or 2 for TRBL_APPLY_SPLIT, 2 for TRBL_APPLY_SPLIT_X4, 1 for
+ * TRBL_APPLY_SPLIT_TMA; any of
+ * 1, 2, 6, 8 for the grouped kernels, which ignore it).  Same rules as trbl_apply_set_rows.  Errors:
  * TRBL_ERR_ARG. */
 int trbl_apply_set_shape(trbl_hamiltonian* h, int kernel, int rows_per_item, int blocks_per_sm);
 

@@ -14,7 +14,7 @@ from ._lib import (  # noqa: F401
     TRBL_OK, TRBL_ERR_ARG, TRBL_ERR_CUDA, TRBL_ERR_OOM, TRBL_ERR_BREAKDOWN, TRBL_ERR_NOCONV,
     TRBL_F32, TRBL_F64, TRBL_PREC_F64, TRBL_PREC_MIXED, TRBL_PROJ_TENSOR, TRBL_PROJ_CUDA_CORE, TRBL_REORTH_SELECTIVE, TRBL_REORTH_TWICE,
     TRBL_NOALLOC_SCRATCH_BYTES,
-    TRBL_APPLY_GROUPED, TRBL_APPLY_FAST, TRBL_APPLY_GROUPED_X2, TRBL_TUNE_CANDIDATES, TrblError,
+    TRBL_APPLY_GROUPED, TRBL_APPLY_FAST, TRBL_APPLY_GROUPED_X2, TRBL_APPLY_SPLIT, TRBL_APPLY_SPLIT_X4, TRBL_APPLY_SPLIT_TMA, TRBL_TUNE_CANDIDATES, TrblError,
     lib, library_path,
     trbl_basis_create, trbl_basis_destroy, trbl_basis_info, trbl_basis_export,
     trbl_basis_export_jumps, trbl_hamiltonian_create, trbl_hamiltonian_destroy,

@@ -15,8 +15,9 @@ TRBL_PREC_F64, TRBL_PREC_MIXED = 1, 2
 TRBL_PROJ_TENSOR, TRBL_PROJ_CUDA_CORE = 0, 1
 TRBL_REORTH_SELECTIVE, TRBL_REORTH_TWICE = 0, 1
 TRBL_NOALLOC_SCRATCH_BYTES = 8 << 20  # include/trbl.h
-TRBL_APPLY_GROUPED, TRBL_APPLY_FAST, TRBL_APPLY_GROUPED_X2 = 0, 1, 2
-TRBL_TUNE_CANDIDATES = 13
+TRBL_APPLY_GROUPED, TRBL_APPLY_FAST, TRBL_APPLY_GROUPED_X2, TRBL_APPLY_SPLIT, TRBL_APPLY_SPLIT_X4, TRBL_APPLY_SPLIT_TMA = \
+    0, 1, 2, 3, 4, 5
+TRBL_TUNE_CANDIDATES = 15
 
 
 class TrblError(RuntimeError):

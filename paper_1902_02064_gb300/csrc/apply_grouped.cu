@@ -90,7 +90,8 @@ __device__ __forceinline__ double flip(double c, int neg) {
 
 template <typename T, int LPE, int CPL>
 __device__ __forceinline__ void grouped_body(const DevH<T>& h, const DevG<T>& g, int item_index,
-                                             const T* __restrict__ V, int64_t ldv, T* __restrict__ W, int64_t ldw) {
+                                             const T* __restrict__ V, int64_t ldv, T* __restrict__ W, int64_t ldw,
+                                             int skip_pn) {
   constexpr int VPL = Vec16<T>::N;  // values per 16-byte chunk
   constexpr int G = 32 / LPE;       // element groups per warp
   constexpr int CW = VPL * LPE;     // values covered by one chunk across the group
@@ -126,7 +127,7 @@ __device__ __forceinline__ void grouped_body(const DevH<T>& h, const DevG<T>& g,
     nq[0] = h.hoffA[pA + 1] - h.hoffA[pA];
   }
   __syncthreads();
-  for (int di = 0; di < ND; ++di) {
+  for (int di = 0; di < ND && !skip_pn; ++di) {
     const int cnt = pstart[di + 1] - pstart[di];
     if (cnt == 0) continue;
     const int sb = h.srcblk[blk * ND + di];
@@ -192,7 +193,8 @@ __device__ __forceinline__ void grouped_body(const DevH<T>& h, const DevG<T>& g,
     // neutron jump of the row is one task; a task runs over the proton jumps
     // of the opposite transfer class.  The staged coefficients carry the
     // proton sign, the neutron sign is the low bit of the jump's op.
-    {
+    // Skipped when the source-stationary kernel (apply_pn.cu) adds this term.
+    if (!skip_pn) {
       const int e1 = h.jsegB[int64_t(pB + 1) * ND];
       for (int e = h.jsegB[int64_t(pB) * ND] + grp; e < e1; e += G) {
         const int2 jb = g.jB2[e];
@@ -235,8 +237,9 @@ __device__ __forceinline__ void grouped_body(const DevH<T>& h, const DevG<T>& g,
 
 template <typename T, int LPE, int CPL>
 __global__ void __launch_bounds__(kThreads, MinBlocks<T, CPL>::value) apply_grouped_kernel(DevH<T> h, DevG<T> g, const T* __restrict__ V,
-                                                                 int64_t ldv, T* __restrict__ W, int64_t ldw) {
-  grouped_body<T, LPE, CPL>(h, g, blockIdx.x, V, ldv, W, ldw);
+                                                                 int64_t ldv, T* __restrict__ W, int64_t ldw,
+                                                                 int skip_pn) {
+  grouped_body<T, LPE, CPL>(h, g, blockIdx.x, V, ldv, W, ldw, skip_pn);
 }
 
 // Several Hamiltonians, on one basis or on bases of different dimension:
@@ -250,7 +253,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T, CPL>::value)
   if (int(blockIdx.x) >= gs[blockIdx.y].nwork) return;
   const DevH<T> h = hs[blockIdx.y];
   const DevG<T> g = gs[blockIdx.y];
-  grouped_body<T, LPE, CPL>(h, g, blockIdx.x, Vs[blockIdx.y], ldv, Ws[blockIdx.y], ldw);
+  grouped_body<T, LPE, CPL>(h, g, blockIdx.x, Vs[blockIdx.y], ldv, Ws[blockIdx.y], ldw, 0);
 }
 
 size_t smem_bytes(int maxP, int maxQ, int maxK, int ND, size_t tsize) {
@@ -259,14 +262,15 @@ size_t smem_bytes(int maxP, int maxQ, int maxK, int ND, size_t tsize) {
 }
 
 template <typename T, int LPE, int CPL>
-int launch_lpe(const DevH<T>& h, const DevG<T>& g, const T* V, int64_t ldv, T* W, int64_t ldw, cudaStream_t s) {
+int launch_lpe(const DevH<T>& h, const DevG<T>& g, const T* V, int64_t ldv, T* W, int64_t ldw, cudaStream_t s,
+               int skip_pn) {
   const size_t sm = smem_bytes(g.maxP, g.maxQ, g.maxK, h.ND, sizeof(T));
   // opt in once to the largest dynamic shared memory a block may use (thread-safe initialisation)
   static const cudaError_t cfg = cudaFuncSetAttribute(apply_grouped_kernel<T, LPE, CPL>,
                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
   TRBL_CUDA(cfg);
   if (sm > size_t(kMaxSmem)) return fail(TRBL_ERR_ARG, "product needs %zu bytes of shared memory", sm);
-  apply_grouped_kernel<T, LPE, CPL><<<g.nwork, kThreads, sm, s>>>(h, g, V, ldv, W, ldw); note_launch();
+  apply_grouped_kernel<T, LPE, CPL><<<g.nwork, kThreads, sm, s>>>(h, g, V, ldv, W, ldw, skip_pn); note_launch();
   TRBL_CUDA(cudaGetLastError());
   return TRBL_OK;
 }
@@ -275,7 +279,7 @@ int launch_lpe(const DevH<T>& h, const DevG<T>& g, const T* V, int64_t ldv, T* W
 // CPL 16-byte chunks per lane.
 template <typename T>
 int launch_typed(const trbl_hamiltonian* hm, const DevH<T>& h, const DevG<T>& g, const T* V, int64_t ldv, T* W,
-                 int64_t ldw, int q, cudaStream_t s) {
+                 int64_t ldw, int q, cudaStream_t s, int skip_pn = 0) {
   const int bytes = q * int(sizeof(T));
   if (bytes % 16) return -1;
   if ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(W)) & 15) return -1;
@@ -284,14 +288,14 @@ int launch_typed(const trbl_hamiltonian* hm, const DevH<T>& h, const DevG<T>& g,
   // TRBL_APPLY_GROUPED_X2: half the lanes per element, two 16-byte chunks
   // each (twice the elements in flight per warp instruction, half the
   // loads per lane group)
-  const bool x2 = hm->apply_kernel == TRBL_APPLY_GROUPED_X2;
+  const bool x2 = hm->apply_kernel == TRBL_APPLY_GROUPED_X2 && !skip_pn;
   switch (bytes / 16) {
-    case 1: return launch_lpe<T, 1, 1>(h, g, V, ldv, W, ldw, s);
-    case 2: return x2 ? launch_lpe<T, 1, 2>(h, g, V, ldv, W, ldw, s) : launch_lpe<T, 2, 1>(h, g, V, ldv, W, ldw, s);
-    case 4: return x2 ? launch_lpe<T, 2, 2>(h, g, V, ldv, W, ldw, s) : launch_lpe<T, 4, 1>(h, g, V, ldv, W, ldw, s);
-    case 8: return x2 ? launch_lpe<T, 4, 2>(h, g, V, ldv, W, ldw, s) : launch_lpe<T, 8, 1>(h, g, V, ldv, W, ldw, s);
-    case 16: return launch_lpe<T, 4, 4>(h, g, V, ldv, W, ldw, s);
-    case 32: return launch_lpe<T, 4, 8>(h, g, V, ldv, W, ldw, s);
+    case 1: return launch_lpe<T, 1, 1>(h, g, V, ldv, W, ldw, s, skip_pn);
+    case 2: return x2 ? launch_lpe<T, 1, 2>(h, g, V, ldv, W, ldw, s, skip_pn) : launch_lpe<T, 2, 1>(h, g, V, ldv, W, ldw, s, skip_pn);
+    case 4: return x2 ? launch_lpe<T, 2, 2>(h, g, V, ldv, W, ldw, s, skip_pn) : launch_lpe<T, 4, 1>(h, g, V, ldv, W, ldw, s, skip_pn);
+    case 8: return x2 ? launch_lpe<T, 4, 2>(h, g, V, ldv, W, ldw, s, skip_pn) : launch_lpe<T, 8, 1>(h, g, V, ldv, W, ldw, s, skip_pn);
+    case 16: return launch_lpe<T, 4, 4>(h, g, V, ldv, W, ldw, s, skip_pn);
+    case 32: return launch_lpe<T, 4, 8>(h, g, V, ldv, W, ldw, s, skip_pn);
     default: return -1;
   }
 }
@@ -341,9 +345,17 @@ int launch_grouped_batch(const void* hs_dev, const void* gs_dev, int nset, int n
                             static_cast<float* const*>(const_cast<void*>(Ws)), ldw, q, s);
 }
 
+int launch_grouped_like(const trbl_hamiltonian* h, const float* V, int64_t ldv, float* W, int64_t ldw, int q,
+                        cudaStream_t s) {
+  if (!h->garena || h->g32.nwork == 0) return -1;
+  return launch_typed<float>(h, h->d32, h->g32, V, ldv, W, ldw, q, s, 1);
+}
+
 int launch_grouped(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, int64_t ldw, int q, int dtype,
                    cudaStream_t s) {
   if (!h->garena || h->g32.nwork == 0) return -1;
+  const int sp = launch_split(h, V, ldv, W, ldw, q, dtype, s);
+  if (sp != -1) return sp;
   const int f = launch_fast(h, V, ldv, W, ldw, q, dtype, s);
   if (f != -1) return f;
   if (dtype == TRBL_F64)
@@ -446,6 +458,8 @@ int upload_grouped(trbl_hamiltonian* h) {
   fill(h->g32, o_c32);
   h->g64.likeB = nullptr;
   h->g32.likeB = reinterpret_cast<const int2*>(base + o_lB);
+  const int rc = upload_pn(h, kidx, ncls, maxK);
+  if (rc) return rc;
   return set_work_items(h, kRowsPerItem);
 }
 
@@ -485,7 +499,7 @@ int set_work_items(trbl_hamiltonian* h, int rows_per_item) {
   h->rows_per_item = rows_per_item;
   h->g64.work = h->g32.work = static_cast<const int4*>(p);
   h->g64.nwork = h->g32.nwork = int(work.size());
-  return TRBL_OK;
+  return set_pn_slabs(h);
 }
 
 }  // namespace trbl

@@ -420,8 +420,10 @@ extern "C" int trbl_hamiltonian_create(const trbl_basis* b, const double* h1A, c
 
 extern "C" void trbl_hamiltonian_destroy(trbl_hamiltonian* h) {
   if (!h) return;
-  if (h->arena || h->garena || h->grad || h->gwork) cudaDeviceSynchronize();
+  if (h->arena || h->garena || h->grad || h->gwork || h->pnarena || h->pnslabs) cudaDeviceSynchronize();
   if (h->gwork) cudaFree(h->gwork);
+  if (h->pnslabs) cudaFree(h->pnslabs);
+  if (h->pnarena) cudaFree(h->pnarena);
   if (h->grad) trbl_grad_state_free(h->grad);
   if (h->arena) cudaFree(h->arena);
   if (h->garena) cudaFree(h->garena);

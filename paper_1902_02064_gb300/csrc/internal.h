@@ -102,6 +102,19 @@ struct DevG {
   const int2* likeB;    // FP32 tables only: species-B like-particle rows as (source local index, FP32 coefficient bits)
 };
 
+// Tables of the source-stationary cross-species kernel (apply_pn.cu).
+struct DevPN {
+  const int32_t* oseg;  // outgoing neutron jumps of source determinant n (global) with transfer index tn:
+                        // entries [oseg[n*ND+tn], oseg[n*ND+tn+1])
+  const int32_t* jout;  // (target local index in its 2M group << 8) | (k << 1) | negative, k = pair index in its class
+  const int32_t* ncls;  // [ND] neutron pairs (b, d) per transfer class
+  const int2* slabs;    // target slabs (A determinant, block), largest first
+  int nslab;
+  int maxPc;            // largest number of proton jumps into one determinant from one transfer class
+  int nbmax;            // largest neutron group of a block
+  int maxCoef;          // largest sum over classes of (proton jumps x pairs of the class) of one determinant
+};
+
 }  // namespace trbl
 
 struct trbl_hamiltonian {
@@ -119,6 +132,9 @@ struct trbl_hamiltonian {
   trbl::DevG<float> g32;
   void* garena = nullptr;
   void* gwork = nullptr;   // work items of the grouped kernel
+  trbl::DevPN pn{};        // source-stationary cross-species kernel (pn.oseg null: not available)
+  void* pnarena = nullptr;
+  void* pnslabs = nullptr;
   int rows_per_item = 0;   // neutron rows per work item (autotuned)
   int apply_kernel = TRBL_APPLY_FAST;  // FP32 product: TRBL_APPLY_FAST where it applies, else the grouped kernel
   int blocks_per_sm = 8;   // resident thread blocks per SM the FP32 fast kernel is compiled for (8 or 6)
@@ -136,6 +152,29 @@ namespace trbl {
 int upload_tables(trbl_hamiltonian* h);
 // Builds and uploads the grouped-kernel tables (apply_grouped.cu).
 int upload_grouped(trbl_hamiltonian* h);
+// Builds and uploads the source-stationary cross-species tables
+// (apply_pn.cu); kidx[b*nB+d] = index of the neutron pair (b, d) in its
+// transfer class, ncls = pairs per class.  Leaves the kernel unavailable
+// (h->pn.oseg null) when its shared memory would not fit.
+int upload_pn(trbl_hamiltonian* h, const std::vector<int>& kidx, const std::vector<int>& ncls, int maxK);
+// Replaces the source-stationary kernel's list of target slabs (those inside
+// the Hamiltonian's row range).
+int set_pn_slabs(trbl_hamiltonian* h);
+// The split product (like-particle terms by the grouped kernel, then the
+// cross-species term by the source-stationary kernel) when h->apply_kernel
+// is TRBL_APPLY_SPLIT and it applies; -1 (nothing launched) otherwise.
+int launch_split(const trbl_hamiltonian* h, const void* V, int64_t ldv, void* W, int64_t ldw, int q, int dtype,
+                 cudaStream_t s);
+// Floats per stage of the staged cross-term kernel for h; 0 when its shared
+// memory does not fit.
+int pn_tma_stage_floats(const trbl_hamiltonian* h);
+// Wait-timeout word of the staged cross-term kernel (stream-ordered copy to
+// host memory).
+int pn_tma_error_to_host(int* host, cudaStream_t s);
+// The grouped kernel without the cross-species term (FP32); -1 when it does
+// not apply.
+int launch_grouped_like(const trbl_hamiltonian* h, const float* V, int64_t ldv, float* W, int64_t ldw, int q,
+                        cudaStream_t s);
 // Replaces the grouped kernel's work items (rows_per_item rows each), for
 // the target slabs inside the Hamiltonian's row range.
 int set_work_items(trbl_hamiltonian* h, int rows_per_item);

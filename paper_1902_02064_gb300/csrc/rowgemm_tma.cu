@@ -165,8 +165,9 @@ int launch_np(const CUtensorMap& map, int K, const double* U, int64_t ldu, int n
 
 }  // namespace
 
-int make_tmap_2d_f32(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint64_t ld,
-                     uint32_t box_cols, uint32_t box_rows) {
+namespace {
+int encode_tmap_2d_f32(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint64_t ld,
+                       uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle swizzle) {
   using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -184,10 +185,21 @@ int make_tmap_2d_f32(CUtensorMap* map, const void* base, uint64_t cols, uint64_t
   const cuuint32_t box[2] = {box_cols, box_rows};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(TRBL_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
   return TRBL_OK;
+}
+}  // namespace
+
+int make_tmap_2d_f32(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint64_t ld,
+                     uint32_t box_cols, uint32_t box_rows) {
+  return encode_tmap_2d_f32(map, base, cols, rows, ld, box_cols, box_rows, CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+int make_tmap_2d_f32_rows(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint64_t ld,
+                          uint32_t box_cols, uint32_t box_rows) {
+  return encode_tmap_2d_f32(map, base, cols, rows, ld, box_cols, box_rows, CU_TENSOR_MAP_SWIZZLE_NONE);
 }
 
 int rowgemm_tma(const float* In, int64_t ldi, int K, const double* U, int64_t ldu, int n, float* Out, int64_t ldo,

@@ -596,6 +596,7 @@ struct Solver {
     TRY(dot_error_to_host(hflags + kTmaErr + 1, s));
     TRY(tc_error_to_host(hflags + kTmaErr + 2, s));
     TRY(wide_error_to_host(hflags + kTmaErr + 3, s));
+    TRY(pn_tma_error_to_host(hflags + kTmaErr + 4, s));
     return TRBL_OK;
   }
 
@@ -603,6 +604,7 @@ struct Solver {
   int wait_errors() {
     if (hflags[kTmaErr] || hflags[kTmaErr + 1] || hflags[kTmaErr + 2] || hflags[kTmaErr + 3])
       return fail(TRBL_ERR_CUDA, "a bounded wait in a projection kernel timed out");
+    if (hflags[kTmaErr + 4]) return fail(TRBL_ERR_CUDA, "a bounded wait in the staged cross-term kernel timed out");
     return TRBL_OK;
   }
 

@@ -20,6 +20,10 @@ constexpr int kErrTmaTimeout = 1;
 // box_rows, 128-byte swizzle, out-of-range elements read as zero.
 int make_tmap_2d_f32(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint64_t ld,
                      uint32_t box_cols, uint32_t box_rows);
+// The same without swizzle: a box lands in shared memory as box_rows rows of
+// box_cols * 4 contiguous bytes.
+int make_tmap_2d_f32_rows(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint64_t ld,
+                          uint32_t box_cols, uint32_t box_rows);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
