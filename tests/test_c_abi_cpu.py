@@ -141,3 +141,20 @@ def test_struct_layouts_match_the_python_binding(tmp_path):
             seen[parts[0]].add(parts[1])
     for name, got in seen.items():
         assert got == {f for f, _ in getattr(_lib, name)._fields_}, name
+
+
+def test_header_constants_match_the_binding():
+    """Every integer constant #defined in include/trbl.h that the Python
+    binding also names has the same value there (status codes, dtypes,
+    precisions, projection and reorthogonalisation modes, product kernels,
+    the autotuner's candidate count, the allocation-free scratch size)."""
+    import re
+    text = open(os.path.join(ROOT, "include", "trbl.h")).read()
+    found = 0
+    for name, value in re.findall(r"^#define (TRBL_[A-Z0-9_]+) (\(?[0-9][0-9u <]*\)?)", text, re.M):
+        if not hasattr(trbl, name):
+            continue
+        expr = value.replace("u", "").strip("()")
+        assert getattr(trbl, name) == eval(expr, {}), name
+        found += 1
+    assert found >= 20
