@@ -417,12 +417,12 @@ int trbl_apply_autotune(trbl_hamiltonian* h, int q, int dtype, float* ms, int* b
 int trbl_apply_set_rows(trbl_hamiltonian* h, int rows_per_item);
 
 /* Sets the whole launch shape: kernel (TRBL_APPLY_GROUPED, TRBL_APPLY_FAST,
- * TRBL_APPLY_GROUPED_X2, TRBL_APPLY_SPLIT or TRBL_APPLY_SPLIT_X4), rows per
- * work item (1..4096) and resident blocks per SM (6 or 8 for the fast
- * kernel, 1 or 2 for TRBL_APPLY_SPLIT, 2 for TRBL_APPLY_SPLIT_X4, 1 for
- * TRBL_APPLY_SPLIT_TMA; any of
- * 1, 2, 6, 8 for the grouped kernels, which ignore it).  Same rules as trbl_apply_set_rows.  Errors:
- * TRBL_ERR_ARG. */
+ * TRBL_APPLY_GROUPED_X2, TRBL_APPLY_SPLIT, TRBL_APPLY_SPLIT_X4 or
+ * TRBL_APPLY_SPLIT_TMA), rows per work item (1..4096) and resident blocks
+ * per SM: 6 or 8 for the fast kernel; 1 or 2 for TRBL_APPLY_SPLIT, 2 for
+ * TRBL_APPLY_SPLIT_X4, 1 for TRBL_APPLY_SPLIT_TMA; any of 1, 2, 6, 8 for
+ * the grouped kernels, which ignore it.  Same rules as
+ * trbl_apply_set_rows.  Errors: TRBL_ERR_ARG. */
 int trbl_apply_set_shape(trbl_hamiltonian* h, int kernel, int rows_per_item, int blocks_per_sm);
 
 /* The current launch shape (any output may be NULL).  Host only. */
