@@ -84,3 +84,35 @@ def test_slab_rows_equal_a_count_from_the_oracle_moves(name):
                     src[where[S ^ (1 << p) ^ (1 << q) ^ (1 << a) ^ (1 << b)]].add(i)
     R = sum(sum(NB[s_] for s_ in src[t]) for t in range(len(dets)) if NB[t] > 0)
     assert bench.slab_rows(bitsA, mA, mB, w.twoM) == R
+
+
+def test_traffic_lookup_is_tied_to_kernel_source_and_shape(tmp_path):
+    """The roofline's DRAM traffic is taken from a committed ncu summary only
+    when the summary names the kernel the bench ran, with its launch shape,
+    and the kernel's source file still hashes to the value stored with the
+    counters; otherwise it is reported as unknown (None).  The split
+    product's figure needs both of its source files unchanged."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1902_02064_gb300", "csrc")
+    sha = lambda f: hashlib.sha256(open(os.path.join(csrc, f), "rb").read()).hexdigest()
+    name = bench.product_kernel_name((0, 16, 8), 32)
+    assert name == "apply_grouped_kernel<float, 8, 1>"
+    p = tmp_path / "traffic.json"
+    p.write_text(json.dumps({"kernel": name, "rows_per_item": 16, "source_sha256": sha("apply_grouped.cu"),
+                             "dram_bytes_per_launch_full_size": 1.5e11}))
+    assert bench.ncu_traffic(name, 16, str(p)) == (1.5e11, name)
+    assert bench.ncu_traffic(name, 64, str(p))[0] is None  # another launch shape
+    assert bench.ncu_traffic(bench.product_kernel_name((1, 16, 8), 32), 16, str(p))[0] is None  # another kernel
+    p.write_text(json.dumps({"kernel": name, "rows_per_item": 16, "source_sha256": "0" * 64,
+                             "dram_bytes_per_launch_full_size": 1.5e11}))
+    assert bench.ncu_traffic(name, 16, str(p))[0] is None  # source changed since the counters
+    split = bench.product_kernel_name((3, 64, 2), 32)
+    assert split == "apply_grouped_kernel<float, 8, 1> + apply_pn_kernel<8, 2, 384, 2>"
+    p.write_text(json.dumps({"kernel": split, "rows_per_item": 64,
+                             "source_sha256": {"apply_grouped.cu": sha("apply_grouped.cu"),
+                                               "apply_pn.cu": sha("apply_pn.cu")},
+                             "dram_bytes_per_launch_full_size": 1.0e11}))
+    assert bench.ncu_traffic(split, 64, str(p)) == (1.0e11, split)
+    p.write_text(json.dumps({"kernel": split, "rows_per_item": 64, "source_sha256": sha("apply_grouped.cu"),
+                             "dram_bytes_per_launch_full_size": 1.0e11}))
+    assert bench.ncu_traffic(split, 64, str(p))[0] is None
