@@ -208,13 +208,15 @@ __global__ void __launch_bounds__(NT, MINB)
 
 // ---------------------------------------------------------------------------
 // Staged form (TRBL_APPLY_SPLIT_TMA).  The source rows of a class are read
-// in chunks of C consecutive source determinants nB: one 2-D TMA box (16
-// columns x C rows) per proton jump of the class lands the C rows of that
+// in chunks of C consecutive source determinants nB: for each proton jump of
+// the class, 2-D TMA boxes of 16 columns x 32 rows land the C rows of that
 // jump's source slab in shared memory, two chunks in flight (a producer warp
 // and full/empty mbarriers).  A consumer warp takes one source row at a time;
 // its 8 lane groups take 8 of the row's outgoing neutron jumps, all reading
 // the same staged 64-byte row (a shared-memory broadcast), so control flow
-// is uniform across the warp and no global load sits on the products' path.
+// is uniform across the warp and V is read from shared memory only.  The
+// row's jump entries still come from global memory, one dependent load per
+// source row, and their latency is what bounds this form.
 // The chunk length is chosen per class so that a chunk fills the stage
 // buffer (C * P * 64 bytes, P proton jumps; C a multiple of the 32-row box,
 // at most 256).  Every mbarrier wait is bounded:
